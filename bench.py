@@ -1,0 +1,419 @@
+#!/usr/bin/env python
+"""Throughput of the adaptive electron sub-cycling push on one or more GB300s.
+
+Workload: 16,777,216 electrons per GPU, Maxwellian (10 keV) initial momenta,
+x0 uniform over 64 wavelengths, in the switched-on plane wave a = 150 sin(xi)
+(E_y = B_z = -da/dxi) sampled on the staggered grid, dt = lambda/75,
+c dt/dx = 0.99, Psi_max = 0.01, third-order temporal interpolation, 20,000
+macro steps in the full run.  A step is one macro step of every electron.
+The timed window starts at --start-step (default 2400: the wave front is in the
+middle of the electron cloud, so each step carries the freshly hit electrons'
+4^5-sub-step pushes as well as the bulk).
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2102_10983_gb300 import workloads as W  # noqa: E402
+
+METRIC = "adaptive-subcycle particle-steps/s, FP32+learned vs plain FP64 at stated error"
+UNIT = "particle-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--start-step", type=int, default=2400)
+    ap.add_argument("--order", type=int, default=3)
+    ap.add_argument("--schedule", default="binned", choices=["plain", "binned"])
+    ap.add_argument("--fp64-steps", type=int, default=200)
+    ap.add_argument("--e2e-steps", type=int, default=300)
+    ap.add_argument("--particles", type=int, default=W.C2.n_particles)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=16384)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- helpers
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if _cuda() else "gloo")
+    return ws, rank, local
+
+
+def _cuda():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, v):
+    if ws <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if _cuda() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def device_levels(wl: W.Workload, n_first: int, n_count: int, device):
+    """Plane-wave levels generated on the device (FP64, same formula as
+    workloads.PlaneWave.field); used only to stage bench inputs in HBM."""
+    import torch
+    n = torch.arange(n_first, n_first + n_count, dtype=torch.float64, device=device)[:, None]
+    i0 = torch.as_tensor(wl.origins(n_first, n_count), dtype=torch.float64, device=device)[:, None]
+    c = torch.arange(wl.window, dtype=torch.float64, device=device)[None, :]
+    wave = wl.wave
+
+    def field(xi):
+        assert wave.profile == "sine"
+        return torch.where(xi > 0, -wave.a0 * torch.cos(xi), torch.zeros_like(xi)) * wave.sign
+
+    E = field(n * wl.dt - (i0 + c) * wl.dx).contiguous()
+    B = field((n + 0.5) * wl.dt - (i0 + c + 0.5) * wl.dx).contiguous()
+    return E, B, wl.origins(n_first, n_count)
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2102_10983_gb300 import native
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    wl = W.Workload(**{**W.C2.__dict__, "n_particles": args.particles, "seed": W.C2.seed + rank,
+                       "order": args.order})
+    p = wl.order
+    start, Wu, K = args.start_step, args.warmup, args.steps
+    last = start + Wu + K
+    n_e = wl.n_particles
+    ini = wl.particles()
+    sched = native.PIC_SCHED_BINNED if args.schedule == "binned" else native.PIC_SCHED_PLAIN
+
+    # all levels -p .. last-1 resident in HBM before anything is timed
+    E, B, i0 = device_levels(wl, -p, last + p, dev)
+    ring = last + p + 1
+
+    def make(precision, schedule, levels_upto):
+        integ = native.Integrator(wl.dt, wl.dx, wl.psi_max, order=p, precision=precision,
+                                  schedule=schedule, capacity=n_e, window=wl.window,
+                                  ring_levels=ring, stream=stream)
+        integ.pic_particles_write(ini.x, ini.px, ini.py, ini.pz)
+        for r in range(levels_upto + p):
+            integ.pic_fields_upload(r - p, int(i0[r]), E[r], B[r])
+        return integ
+
+    out = {}
+    # ---- mixed form: fast-forward, warm up, then K timed steps
+    integ = make(native.PIC_MIXED, sched, last)
+    if start > 0:
+        integ.pic_push_step(0, start, want_stats=False)
+    integ.pic_push_step(start, Wu, want_stats=False)
+    integ.pic_stats_read(reset=True)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = integ.launches()
+    integ.timing(True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    integ.pic_push_step(start + Wu, K, want_stats=False)   # one call: K macro steps
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    total_ms = ev0.elapsed_time(ev1)
+    kern_ms, kern_steps = integ.timing_read()
+    integ.timing(False)
+    launches = integ.launches() - launches0
+    clk = clocks.stop()
+    st = integ.pic_stats_read(reset=True)
+    integ.close()
+    total_ms = max_over_ranks(ws, total_ms)
+    ps = n_e * K * ws / (total_ms / 1e3)
+    substeps = max(st.substeps, 1)
+    out.update(value=ps, ms_per_step=total_ms / K, launches=launches, clocks=clk,
+               kern_ms=kern_ms / max(kern_steps, 1), stats=st.as_dict(),
+               substeps_per_s=st.substeps * ws / (total_ms / 1e3))
+
+    # ---- accuracy and the FP64 form over the same steps (start .. start+Wu+K64)
+    K64 = min(K, args.fp64_steps)
+    if not args.no_fp64:
+        acc_end = start + Wu + K64
+        ref = make(native.PIC_FP64, native.PIC_SCHED_PLAIN, last)
+        ref.pic_push_step(0, start + Wu, want_stats=False)
+        torch.cuda.synchronize()
+        ref.timing(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ref.pic_push_step(start + Wu, K64, want_stats=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        ref.timing(False)
+        ms64 = max_over_ranks(ws, ms64)
+        mix = make(native.PIC_MIXED, sched, last)
+        mix.pic_push_step(0, acc_end, want_stats=False)
+        a = [torch.empty(n_e, dtype=torch.float64, device=dev) for _ in range(4)]
+        b = [torch.empty(n_e, dtype=torch.float64, device=dev) for _ in range(4)]
+        ref.pic_particles_read(*a)
+        mix.pic_particles_read(*b)
+        torch.cuda.synchronize()
+        ref.close()
+        mix.close()
+        x0 = torch.as_tensor(ini.x, device=dev)
+        dpv = torch.stack([(a[q] - b[q]).abs() for q in (1, 2, 3)]).amax(0) / wl.a0 ** 2
+        dp = float(dpv.max())
+        n_out = int((dpv > 1e-4).sum())
+        q9999 = float(torch.quantile(dpv[torch.randperm(n_e, device=dev)[:1 << 20]].float(), 0.9999))
+        ga = torch.sqrt(1 + a[1] ** 2 + a[2] ** 2 + a[3] ** 2) - 1
+        gb = torch.sqrt(1 + b[1] ** 2 + b[2] ** 2 + b[3] ** 2) - 1
+        de = abs(float(ga.mean() - gb.mean())) / float(ga.mean())
+        disp = float(((a[0] - b[0]).abs() / torch.clamp((a[0] - x0).abs(), min=1.0)).max())
+        out.update(fp64_value=n_e * K64 * ws / (ms64 / 1e3), fp64_ms_per_step=ms64 / K64,
+                   fp64_steps=K64,
+                   accuracy={"vs": "FP64 GPU form (bit-identical to the FP64 oracle)",
+                             "at_step": acc_end, "max_dp_over_a0sq": dp,
+                             "electrons_over_1e-4": n_out, "p99.99_dp_over_a0sq": q9999,
+                             "energy_gain_rel_diff": de, "max_rel_displacement_err": disp})
+
+    # ---- end to end through the C ABI with host buffers
+    if not args.no_e2e:
+        Ke = min(K, args.e2e_steps)
+        integ = make(native.PIC_MIXED, sched, start + Wu)
+        integ.pic_push_step(0, start + Wu, want_stats=False)
+        hostE = torch.empty((Ke, wl.window), dtype=torch.float64).pin_memory()
+        hostB = torch.empty((Ke, wl.window), dtype=torch.float64).pin_memory()
+        hostE.copy_(E[p + start + Wu: p + start + Wu + Ke].cpu())
+        hostB.copy_(B[p + start + Wu: p + start + Wu + Ke].cpu())
+        torch.cuda.synchronize()
+        barrier(ws)
+        t0 = time.perf_counter()
+        for r in range(Ke):
+            s = start + Wu + r
+            integ.pic_fields_upload(s, int(i0[s + p]), hostE[r], hostB[r])
+            integ.pic_push_step(s, 1, want_stats=True,
+                                ok=(native.PIC_OK, native.PIC_ERANGE, native.PIC_EKMAX))
+        t1 = time.perf_counter()
+        barrier(ws)
+        integ.close()
+        e2e_s = max_over_ranks(ws, t1 - t0)
+        out["e2e"] = {"value": n_e * Ke * ws / e2e_s, "unit": UNIT, "steps": Ke,
+                      "h2d_bytes_per_step": 2 * wl.window * 8,
+                      "d2h_bytes_per_step": int(native.ctypes.sizeof(native.PicStepStats))}
+    return wl, out
+
+
+def cpu_baseline(wl: W.Workload, n_sample: int, steps: int):
+    """The oracle, as it stands, on one host core: the first n_sample electrons
+    of the workload through its first `steps` macro steps."""
+    import oracle
+    p = wl.order
+    prm = oracle.Params(dt=wl.dt, dx=wl.dx, psi_max=wl.psi_max, order=p)
+    ini = wl.particles(n_sample)
+    parts = oracle.Particles(ini.x, ini.px, ini.py, ini.pz)
+    oracle.lib()
+    t_cpu = 0.0
+    done = 0
+    st = oracle.OrcStats()
+    while done < steps:
+        c = min(500, steps - done)
+        E, B, i0 = wl.levels(done - p, c + p)
+        t0 = time.perf_counter()
+        oracle.run(prm, parts, E, i0, B, i0, st)
+        t_cpu += time.perf_counter() - t0
+        done += c
+    return n_sample * steps / t_cpu, st
+
+
+def run_reference(args, ws, rank):
+    """The CPU oracle as the reference arm (rank 0 only)."""
+    wl = W.C2
+    if rank != 0:
+        return None
+    import oracle
+    p = wl.order
+    n_s = args.cpu_sample
+    prm = oracle.Params(dt=wl.dt, dx=wl.dx, psi_max=wl.psi_max, order=p)
+    ini = wl.particles(n_s)
+    parts = oracle.Particles(ini.x, ini.px, ini.py, ini.pz)
+    oracle.lib()
+    start, Wu, K = args.start_step, args.warmup, args.steps
+    # the sample walks from step 0; only steps start+Wu .. start+Wu+K are timed
+    E, B, i0 = wl.levels(-p, start + Wu + K + p)
+    if start + Wu > 0:
+        oracle.run(prm, parts, E[: start + Wu + p], i0[: start + Wu + p],
+                   B[: start + Wu + p], i0[: start + Wu + p])
+    t0 = time.perf_counter()
+    for s in range(start + Wu, start + Wu + K):
+        r = s  # row of level s - p
+        oracle.run(prm, parts, E[r: r + p + 1], i0[r: r + p + 1], B[r: r + p + 1], i0[r: r + p + 1])
+    el = time.perf_counter() - t0
+    v = n_s * K / el
+    return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": K,
+            "warmup": Wu, "ms_per_step": el * 1e3 / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": wl.name + f" (oracle sample: first {n_s} electrons)",
+                       "start_step": start},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"first {n_s} of {wl.n_particles} electrons, steps "
+                                       f"{start + Wu}..{start + Wu + K - 1}"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        line = run_reference(args, ws, rank)
+        if line is not None:
+            print(json.dumps(line))
+        return
+    wl, out = run_ours(args, ws, rank, local)
+    if rank != 0:
+        return
+    hbm, peak_src = measured_peaks()
+    # algorithmic bytes of the mixed push per particle-step: cell i32 + frac f32 +
+    # p 3 x f32 + status u8, read and written
+    bytes_per = 2 * (4 + 4 + 12 + 1)
+    achieved = bytes_per * wl.n_particles / (out["kern_ms"] / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": out["value"], "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "electrons_per_gpu": wl.n_particles, "a0": wl.a0,
+                   "dt": "lambda/75", "c_dt_over_dx": 0.99, "psi_max": wl.psi_max,
+                   "order": wl.order, "form": "mixed", "schedule": args.schedule,
+                   "start_step": args.start_step,
+                   "l2": "inputs larger than L2 (352 MB particle state per GPU)",
+                   "parallelism": f"replicas x{ws}"},
+        "substeps_per_s": out["substeps_per_s"],
+        "fp64_value": out.get("fp64_value"), "fp64_steps": out.get("fp64_steps"),
+        "speedup_vs_fp64": (out["value"] / out["fp64_value"]) if out.get("fp64_value") else None,
+        "accuracy": out.get("accuracy"),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "peak_source": peak_src, "kernel": "push_mixed (per step)",
+                     "bytes_per_particle_step": bytes_per},
+        "gpu_launches": out["launches"], "clocks": out["clocks"],
+        "k_hist": out["stats"]["k_hist"],
+    }
+    if "e2e" in out:
+        line["e2e"] = out["e2e"]
+    if not args.no_cpu_baseline:
+        v, _ = cpu_baseline(wl, args.cpu_sample, 1000)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"first {args.cpu_sample} electrons x steps 0..999 "
+                                          f"of the same workload, serial FP64"}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,170 @@
+/*
+ * pic_gb300.h -- C ABI of the GB300 (sm_103a) adaptive electron sub-cycling
+ * particle integrator of Tangtartharakul, Chen and Arefiev, "Particle
+ * integrator for particle-in-cell simulations of ultra-high intensity
+ * laser-plasma interactions" (arXiv 2102.10983).
+ *
+ * Problem statement (Secs. II-IV): normalized units omega = c = m = |e| = 1
+ * (time 1/omega, length c/omega, momentum m c, fields m omega c/|e|); a 1D
+ * staggered Yee grid carrying E_y and B_z only; per electron, each macro step
+ * dt picks k from the rotation-angle criterion |Psi| <= Psi_max (Sec. IV,
+ * Algorithm 1), then takes m = 4^k Boris sub-steps h = dt/4^k (Sec. III,
+ * Eqs. eq:p - eq:x), the first with the transitional step (h_old + h)/2, each
+ * with E_y and B_z interpolated in time by order-p Lagrange polynomials over
+ * the stored field levels (Sec. VI, Eqs. eq:lagrange1-2 - eq:lagrange2-3) and
+ * in space by the tent shape function (Sec. III, Eqs. eq:Enp, eq:Bnp).
+ *
+ * Grid convention: E_y lives on nodes x = i dx at times n dt ("level n"); B_z
+ * lives on nodes x = (i + 1/2) dx at times (n + 1/2) dt (uploaded together with
+ * E level n).  This is the paper's staggering shifted by half a cell.
+ *
+ * Conventions of every call:
+ *  - Return value: PIC_OK (0) or one of the PIC_E* codes below.  No call
+ *    throws; pic_last_error() gives a static, human-readable reason.
+ *  - Pointers marked "where" are host pointers (PIC_HOST) or device pointers
+ *    of the current CUDA device (PIC_DEVICE).  They are borrowed: the caller
+ *    owns them and they need only stay valid until the call returns (host) or
+ *    until the work queued on the context's stream has finished (device).
+ *  - The context owns its particle store, its field ring and its counters; it
+ *    allocates them in pic_create and frees them in pic_destroy.
+ *  - All work is queued on the context's stream (a cudaStream_t passed as
+ *    void*, NULL = legacy default stream).  Calls with host destinations, and
+ *    pic_push_step with a non-NULL stats pointer, synchronize that stream.
+ *  - A context is not thread-safe; one host thread drives it at a time.
+ */
+#ifndef PIC_GB300_H
+#define PIC_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define PIC_OK 0
+#define PIC_EINVAL 1    /* bad argument (sizes, orders, pointers, missing levels) */
+#define PIC_ENOMEM 2    /* device or host allocation failed                        */
+#define PIC_ECUDA 3     /* a CUDA runtime call failed                              */
+#define PIC_ERANGE 4    /* particles left the field window this step (frozen)      */
+#define PIC_EKMAX 5     /* the criterion was capped at k_max for some particle     */
+#define PIC_ETIMEOUT 6  /* a bounded device-side wait gave up                      */
+
+/* memory spaces */
+#define PIC_HOST 0
+#define PIC_DEVICE 1
+
+/* arithmetic forms */
+#define PIC_FP64 0   /* all-FP64 push; matches the FP64 oracle bit for bit       */
+#define PIC_MIXED 1  /* FP32 interpolation, rotation and criterion; position kept
+                        as an exact integer cell plus an FP32 in-cell offset      */
+
+/* schedules of the push (how uneven sub-cycle counts are spread over warps) */
+#define PIC_SCHED_PLAIN 0   /* one thread per particle, no binning               */
+#define PIC_SCHED_BINNED 1  /* m = 1 particles streamed; k > 0 particles compacted
+                               by warp ballot into per-k queues and drained by
+                               warps of equal k                                   */
+
+/* per-particle status byte: low 7 bits = k of the last macro step; bit 7 set =
+   the particle left the field window and is frozen */
+#define PIC_STATUS_LOST 0x80
+
+typedef struct {
+  double dt;          /* macro step (the field solver's step), > 0               */
+  double dx;          /* cell size, > 0                                          */
+  double psi_max;     /* rotation-angle threshold Psi_max, > 0 (Sec. IV)         */
+  double qm;          /* charge/mass in units of |e|/m; -1 for the electron      */
+  int32_t order;      /* Lagrange order p, 1..5 (Sec. VI); p+1 levels are used   */
+  int32_t k_max;      /* cap on k, 0..7; m <= 4^k_max                            */
+  int32_t precision;  /* PIC_FP64 or PIC_MIXED                                   */
+  int32_t field_time; /* 0: sub-step fields at the position time t_n + (j-1)h;
+                         1: at the middle of the j-th sub-interval of
+                            [t_n - dt/2, t_n + dt/2]                              */
+  int32_t schedule;   /* PIC_SCHED_*                                             */
+  int32_t reserved[3];
+} pic_params;
+
+typedef struct {
+  int64_t k_hist[8];      /* macro steps taken with each k                       */
+  int64_t substeps;       /* Boris sub-steps taken (sum of m)                     */
+  int64_t n_star;         /* sub-steps of macro steps with k > 0 (Sec. VII)       */
+  int64_t clamped;        /* macro steps whose k was capped at k_max              */
+  int64_t out_of_window;  /* particles frozen because they left the window        */
+  int32_t error;          /* device error word (0 = none)                         */
+  int32_t reserved;
+} pic_step_stats;
+
+typedef struct pic_ctx pic_ctx;
+
+/* Create a context for up to `capacity` particles and a field window of
+ * `window_cells` nodes (a power of two, >= 16) held for `ring_levels` time
+ * levels (>= order + 1; more levels let several steps run per call).
+ * `stream` is a cudaStream_t (or NULL).  On success *out receives the context.
+ * Errors: PIC_EINVAL (parameters out of range), PIC_ENOMEM, PIC_ECUDA. */
+int pic_create(const pic_params* prm, int64_t capacity, int64_t window_cells,
+               int32_t ring_levels, void* stream, pic_ctx** out);
+
+/* Free everything the context owns.  NULL is accepted. */
+int pic_destroy(pic_ctx* ctx);
+
+/* Load n particles (n <= capacity): position x at t_n, momentum (px, py, pz)
+ * at t_n - h_old/2, and the status byte (k_prev | PIC_STATUS_LOST); status may
+ * be NULL (all k_prev = 0, i.e. h_old = dt).  All arrays have n FP64 (status:
+ * uint8) entries in `where` memory.  In PIC_MIXED form x is split on the device
+ * into an integer cell and an FP32 offset, and p is rounded to FP32.
+ * Errors: PIC_EINVAL, PIC_ECUDA. */
+int pic_particles_write(pic_ctx* ctx, const double* x, const double* px, const double* py,
+                        const double* pz, const uint8_t* status, int64_t n, int32_t where);
+
+/* Copy the first n particles out (FP64; status as above).  Any output pointer
+ * may be NULL to skip it.  Synchronizes the stream when where == PIC_HOST.
+ * Errors: PIC_EINVAL, PIC_ECUDA. */
+int pic_particles_read(pic_ctx* ctx, double* x, double* px, double* py, double* pz,
+                       uint8_t* status, int64_t n, int32_t where);
+
+/* Store field level `level`: Ey = E_y at t = level*dt on nodes i0 .. i0+W-1 and
+ * Bz = B_z at t = (level + 1/2) dt on nodes i0+1/2 .. i0+W-1/2 (W = the
+ * context's window), each W FP64 values in `where` memory.  The level replaces
+ * the oldest one in the ring (slot level mod ring_levels).  (Eqs. eq:Ey,
+ * eq:Bz give the staggering; Sec. VI the history the interpolation needs.)
+ * Errors: PIC_EINVAL, PIC_ECUDA. */
+int pic_fields_upload(pic_ctx* ctx, int64_t level, int64_t i0, const double* Ey,
+                      const double* Bz, int32_t where);
+
+/* Advance all loaded particles through macro steps n .. n+n_steps-1 (each one
+ * is Algorithm 1 of Sec. IV with the order-p interpolation of Sec. VI).  Step
+ * s needs levels s-p .. s in the ring (error PIC_EINVAL otherwise).  If stats
+ * is non-NULL the stream is synchronized, the counters of these steps are
+ * returned and reset, and PIC_ERANGE / PIC_EKMAX report frozen or capped
+ * particles (the step still completes for all others).  With stats == NULL
+ * nothing synchronizes and the counters keep accumulating (pic_stats_read).
+ * Errors: PIC_EINVAL, PIC_ECUDA, PIC_ERANGE, PIC_EKMAX, PIC_ETIMEOUT. */
+int pic_push_step(pic_ctx* ctx, int64_t n, int64_t n_steps, pic_step_stats* stats);
+
+/* Read (and optionally reset) the accumulated counters.  Synchronizes. */
+int pic_stats_read(pic_ctx* ctx, pic_step_stats* stats, int32_t reset);
+
+/* Replace the stream on which the context queues its work. */
+int pic_set_stream(pic_ctx* ctx, void* stream);
+
+/* Turn CUDA-event timing of the push on (1) or off (0).  When on, every step
+ * of pic_push_step is bracketed by two events recorded on the context's
+ * stream, around the push kernel launches of that step only.  Errors:
+ * PIC_EINVAL, PIC_ECUDA. */
+int pic_timing_enable(pic_ctx* ctx, int32_t on);
+
+/* Sum of the bracketed durations (milliseconds) and the number of timed steps
+ * since the last reset; synchronizes the stream.  Errors: PIC_EINVAL, PIC_ECUDA. */
+int pic_timing_read(pic_ctx* ctx, double* total_ms, int64_t* steps, int32_t reset);
+
+/* Number of kernel launches the context has queued since creation. */
+int64_t pic_launch_count(const pic_ctx* ctx);
+
+/* Static reason for the last error on this context (or of pic_create when
+ * ctx is NULL). */
+const char* pic_last_error(const pic_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIC_GB300_H */

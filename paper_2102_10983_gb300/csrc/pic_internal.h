@@ -1,0 +1,94 @@
+// Internal declarations shared by the translation units of libpic_gb300.so.
+// Nothing here is part of the public ABI (include/pic_gb300.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pic_gb300.h"
+
+namespace pic {
+
+constexpr int kMaxOrder = 5;
+constexpr int kMaxK = 7;
+
+// Device counters of one context (accumulated by every push launch).
+struct DevStats {
+  unsigned long long k_hist[8];
+  unsigned long long substeps;
+  unsigned long long n_star;
+  unsigned long long clamped;
+  unsigned long long lost;
+  int error;
+  int pad;
+};
+
+// Row of the weight table for sub-step j (1-based) of a macro step with
+// exponent k: rows are grouped by k, 4^k rows per k.
+__host__ __device__ inline int64_t wrow(int k, int64_t j) {
+  return (((int64_t)1 << (2 * k)) - 1) / 3 + (j - 1);
+}
+inline int64_t wrows_total(int k_max) { return wrow(k_max + 1, 1) + 1; }  // + criterion row
+
+// Arguments of the FP64 push (one macro step).
+struct PushArgsF64 {
+  int64_t n;
+  double* x;
+  double* px;
+  double* py;
+  double* pz;
+  uint8_t* status;
+  const double* E[kMaxOrder + 1];  // ring slot of level n-p+l, l = 0..p
+  const double* B[kMaxOrder + 1];
+  double lo, hi;  // s = x/dx must satisfy lo <= s < hi (and s - 1/2 too)
+  int64_t mask;   // W - 1
+  double dt, inv_dx, psi_max, qm, qm_abs;
+  int k_max;
+  const double* wtab;  // rows of [E weights p+1 | B weights p+1]
+  int64_t crit_row;
+  DevStats* stats;
+};
+
+// Arguments of the mixed-precision push.  Position = (cell + frac) * dx with
+// an exact int32 cell and an FP32 offset.
+struct PushArgsMixed {
+  int64_t n;
+  int32_t* cell;
+  float* frac;
+  float* px;
+  float* py;
+  float* pz;
+  uint8_t* status;
+  const float* E[kMaxOrder + 1];   // this step's levels n-p .. n
+  const float* B[kMaxOrder + 1];
+  const float* Ep[kMaxOrder + 1];  // previous step's levels (binned: deferred work)
+  const float* Bp[kMaxOrder + 1];
+  int32_t lo, hi;      // tent node j must satisfy lo <= j and j+1 <= hi
+  int32_t lo_p, hi_p;  // same for the previous step
+  int32_t mask;
+  float dt, psi_max, qm, qm_abs;
+  float inv_dx;
+  int k_max;
+  const float* wtab;
+  int64_t crit_row;
+  DevStats* stats;
+  // binned schedule: per-k queues (k = 1..7, qcap entries each), double-buffered
+  const int32_t* queue_in;
+  int32_t* queue_out;
+  int32_t* qcount_in;   // [8], consumed by this launch, zeroed by its last block
+  int32_t* qcount_out;  // [8], filled by this launch
+  int64_t qcap;
+  int* cursor;
+  unsigned* blocks_done;
+  int parity_cur, parity_next;
+  int finalize;
+};
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t build_wtab_f64(double* wtab, int order, int k_max, int field_time, cudaStream_t s);
+cudaError_t build_wtab_f32(float* wtab, const double* wtab64, int64_t count, cudaStream_t s);
+cudaError_t launch_push_f64(const PushArgsF64& a, int order, cudaStream_t s, int* launches);
+cudaError_t launch_push_mixed(const PushArgsMixed& a, int order, int schedule, int sm_count,
+                              cudaStream_t s, int* launches);
+
+}  // namespace pic

@@ -1,0 +1,210 @@
+"""Thin ctypes binding of the C ABI in include/pic_gb300.h.
+
+Argument marshalling only: every step of the integrator runs in the CUDA
+kernels of libpic_gb300.so.  The functions keep the C names.  Host arrays are
+numpy arrays; device arrays are torch CUDA tensors (PyTorch provides device
+memory and streams here, nothing else).  There is no CPU fallback: if the
+library is missing or fails to load, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA, PIC_ERANGE, PIC_EKMAX, PIC_ETIMEOUT = range(7)
+PIC_HOST, PIC_DEVICE = 0, 1
+PIC_FP64, PIC_MIXED = 0, 1
+PIC_SCHED_PLAIN, PIC_SCHED_BINNED = 0, 1
+PIC_STATUS_LOST = 0x80
+
+ERR_NAMES = {0: "PIC_OK", 1: "PIC_EINVAL", 2: "PIC_ENOMEM", 3: "PIC_ECUDA", 4: "PIC_ERANGE",
+             5: "PIC_EKMAX", 6: "PIC_ETIMEOUT"}
+
+
+class PicParams(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("dx", ctypes.c_double), ("psi_max", ctypes.c_double),
+                ("qm", ctypes.c_double), ("order", ctypes.c_int32), ("k_max", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("field_time", ctypes.c_int32),
+                ("schedule", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class PicStepStats(ctypes.Structure):
+    _fields_ = [("k_hist", ctypes.c_int64 * 8), ("substeps", ctypes.c_int64),
+                ("n_star", ctypes.c_int64), ("clamped", ctypes.c_int64),
+                ("out_of_window", ctypes.c_int64), ("error", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {"k_hist": list(self.k_hist), "substeps": self.substeps, "n_star": self.n_star,
+                "clamped": self.clamped, "out_of_window": self.out_of_window, "error": self.error}
+
+
+# (name, restype, argtypes) of every symbol declared in include/pic_gb300.h
+_VP, _I32, _I64, _D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+SIGNATURES = {
+    "pic_create": (ctypes.c_int, [ctypes.POINTER(PicParams), _I64, _I64, _I32, _VP,
+                                  ctypes.POINTER(_VP)]),
+    "pic_destroy": (ctypes.c_int, [_VP]),
+    "pic_particles_write": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _I64, _I32]),
+    "pic_particles_read": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _I64, _I32]),
+    "pic_fields_upload": (ctypes.c_int, [_VP, _I64, _I64, _VP, _VP, _I32]),
+    "pic_push_step": (ctypes.c_int, [_VP, _I64, _I64, ctypes.POINTER(PicStepStats)]),
+    "pic_stats_read": (ctypes.c_int, [_VP, ctypes.POINTER(PicStepStats), _I32]),
+    "pic_set_stream": (ctypes.c_int, [_VP, _VP]),
+    "pic_timing_enable": (ctypes.c_int, [_VP, _I32]),
+    "pic_timing_read": (ctypes.c_int, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_I64), _I32]),
+    "pic_launch_count": (ctypes.c_int64, [_VP]),
+    "pic_last_error": (ctypes.c_char_p, [_VP]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libpic_gb300.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        if build_if_missing and _build.needs_build():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"libpic_gb300.so not built ({_build.LIB}); run build()")
+        L = ctypes.CDLL(_build.LIB)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class PicError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _check(code: int, ctx=None, ok=(PIC_OK,)):
+    if code not in ok:
+        raise PicError(code, (lib().pic_last_error(ctx) or b"").decode())
+    return code
+
+
+def _ptr(a):
+    """(address, where) of a numpy array or a torch tensor (None -> NULL)."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data, PIC_HOST
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return a.data_ptr(), (PIC_DEVICE if a.is_cuda else PIC_HOST)
+    raise TypeError(type(a))
+
+
+def _where(*arrs):
+    ws = {w for _, w in (_ptr(a) for a in arrs if a is not None)}
+    if len(ws) != 1:
+        raise ValueError("arrays must all be on the host or all on the device")
+    return ws.pop()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            return 0
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Integrator:
+    """One context of the C library (pic_create ... pic_destroy)."""
+
+    def __init__(self, dt, dx, psi_max, order=3, k_max=7, precision=PIC_FP64, field_time=0,
+                 schedule=PIC_SCHED_PLAIN, qm=-1.0, capacity=0, window=256, ring_levels=None,
+                 stream=None):
+        self.params = PicParams(float(dt), float(dx), float(psi_max), float(qm), int(order),
+                                int(k_max), int(precision), int(field_time), int(schedule))
+        self.window = int(window)
+        self.ring_levels = int(ring_levels if ring_levels is not None else order + 1)
+        self.capacity = int(capacity)
+        h = ctypes.c_void_p()
+        _check(lib().pic_create(ctypes.byref(self.params), self.capacity, self.window,
+                                self.ring_levels, _stream_handle(stream), ctypes.byref(h)))
+        self.ctx = h
+        self.n = 0
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().pic_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        _check(lib().pic_set_stream(self.ctx, _stream_handle(stream)), self.ctx)
+
+    def pic_particles_write(self, x, px, py, pz, status=None):
+        n = int(x.shape[0])
+        w = _where(x, px, py, pz, status)
+        _check(lib().pic_particles_write(self.ctx, _ptr(x)[0], _ptr(px)[0], _ptr(py)[0],
+                                         _ptr(pz)[0], _ptr(status)[0], n, w), self.ctx)
+        self.n = n
+
+    def pic_particles_read(self, x=None, px=None, py=None, pz=None, status=None, n=None):
+        arrs = [a for a in (x, px, py, pz, status) if a is not None]
+        n = self.n if n is None else int(n)
+        w = _where(*arrs)
+        _check(lib().pic_particles_read(self.ctx, _ptr(x)[0], _ptr(px)[0], _ptr(py)[0],
+                                        _ptr(pz)[0], _ptr(status)[0], n, w), self.ctx)
+
+    def pic_fields_upload(self, level, i0, Ey, By):
+        w = _where(Ey, By)
+        assert Ey.shape[-1] == self.window and By.shape[-1] == self.window
+        _check(lib().pic_fields_upload(self.ctx, int(level), int(i0), _ptr(Ey)[0], _ptr(By)[0],
+                                       w), self.ctx)
+
+    def pic_push_step(self, n, n_steps=1, want_stats=True, ok=(PIC_OK,)):
+        st = PicStepStats() if want_stats else None
+        code = lib().pic_push_step(self.ctx, int(n), int(n_steps),
+                                   ctypes.byref(st) if st is not None else None)
+        _check(code, self.ctx, ok=ok)
+        return (st, code) if want_stats else (None, code)
+
+    def pic_stats_read(self, reset=True) -> PicStepStats:
+        st = PicStepStats()
+        _check(lib().pic_stats_read(self.ctx, ctypes.byref(st), 1 if reset else 0), self.ctx)
+        return st
+
+    def timing(self, on: bool = True):
+        _check(lib().pic_timing_enable(self.ctx, 1 if on else 0), self.ctx)
+
+    def timing_read(self, reset: bool = True):
+        ms, steps = ctypes.c_double(), ctypes.c_int64()
+        _check(lib().pic_timing_read(self.ctx, ctypes.byref(ms), ctypes.byref(steps),
+                                     1 if reset else 0), self.ctx)
+        return ms.value, steps.value
+
+    def launches(self) -> int:
+        return int(lib().pic_launch_count(self.ctx))
+
+    # convenience: read everything to numpy
+    def read_numpy(self):
+        n = self.n
+        out = [np.empty(n) for _ in range(4)] + [np.empty(n, np.uint8)]
+        self.pic_particles_read(*out)
+        return out

@@ -52,9 +52,92 @@ def run_oracle_follow(wl: Workload, prm: oracle.Params, parts: oracle.Particles,
         W = 1 << max(4, int(span - 1).bit_length())
         i0 = np.full(c + p, lo, dtype=np.int64)
         from paper_2102_10983_gb300.workloads import sample_levels
-        E, B = sample_levels(wl.wave, wl.dt, wl.dx, n - p, c + p, i0, W)
+        E, B = sample_levels(wl.wave, wl.dt, wl.dx, n - p, c + p, i0, W, rowwise=False)
         oracle.run(prm, parts, E, i0, B, i0, st, r_ref, r_dev)
         done += c
         if on_chunk is not None:
             on_chunk(n + c, parts)
     return st
+
+
+# ---------------------------------------------------------------- CUDA path drivers
+
+def gpu_integrator(wl: Workload, precision: int, order: int | None = None,
+                   psi_max: float | None = None, field_time: int = 0, k_max: int = 7,
+                   schedule: int = 0, capacity: int | None = None, ring_levels: int | None = None):
+    from paper_2102_10983_gb300 import native
+    p = wl.order if order is None else order
+    cap = wl.n_particles if capacity is None else capacity
+    return native.Integrator(wl.dt, wl.dx, wl.psi_max if psi_max is None else psi_max, order=p,
+                             k_max=k_max, precision=precision, field_time=field_time,
+                             schedule=schedule, capacity=cap, window=wl.window,
+                             ring_levels=ring_levels if ring_levels is not None else p + 2)
+
+
+class GpuRun:
+    """Feeds levels to an Integrator: level s is uploaded right before step s."""
+
+    def __init__(self, integ, wl: Workload, order: int):
+        self.integ, self.wl, self.p = integ, wl, order
+        self.next_level = None
+        self.stats = []
+
+    def run(self, n0: int, n_steps: int, chunk: int = 4096, want_stats: bool = True,
+            ok=(0,), on_chunk=None):
+        from paper_2102_10983_gb300 import native
+        p = self.p
+        if self.next_level is None:
+            E, B, i0 = self.wl.levels(n0 - p, p)
+            for r in range(p):
+                self.integ.pic_fields_upload(n0 - p + r, i0[r], E[r], B[r])
+            self.next_level = n0
+        assert self.next_level == n0
+        agg = native.PicStepStats()
+        done = 0
+        while done < n_steps:
+            c = min(chunk, n_steps - done)
+            E, B, i0 = self.wl.levels(n0 + done, c)
+            for r in range(c):
+                s = n0 + done + r
+                self.integ.pic_fields_upload(s, i0[r], E[r], B[r])
+                st, _ = self.integ.pic_push_step(s, 1, want_stats=want_stats, ok=ok)
+                if st is not None:
+                    for k in range(8):
+                        agg.k_hist[k] += st.k_hist[k]
+                    agg.substeps += st.substeps
+                    agg.n_star += st.n_star
+                    agg.clamped += st.clamped
+                    agg.out_of_window += st.out_of_window
+            done += c
+            self.next_level = n0 + done
+            if on_chunk is not None:
+                on_chunk(n0 + done)
+        return agg
+
+
+def run_gpu_calls(integ, wl: Workload, order: int, n0: int, n_steps: int, call_lens,
+                  ok=(0, 4, 5)):
+    """Steps n0..n0+n_steps-1 as pic_push_step calls of the given lengths (cycled);
+    each call's levels are uploaded first (the ring must hold p + 1 + max(call))."""
+    from paper_2102_10983_gb300 import native
+    p = order
+    E, B, i0 = wl.levels(n0 - p, n_steps + p)
+    for r in range(p):
+        integ.pic_fields_upload(n0 - p + r, i0[r], E[r], B[r])
+    agg = native.PicStepStats()
+    s, q = n0, 0
+    while s < n0 + n_steps:
+        c = min(call_lens[q % len(call_lens)], n0 + n_steps - s)
+        q += 1
+        for r in range(c):
+            lev = s + r
+            integ.pic_fields_upload(lev, i0[lev - n0 + p], E[lev - n0 + p], B[lev - n0 + p])
+        st, _ = integ.pic_push_step(s, c, want_stats=True, ok=ok)
+        for k in range(8):
+            agg.k_hist[k] += st.k_hist[k]
+        agg.substeps += st.substeps
+        agg.n_star += st.n_star
+        agg.clamped += st.clamped
+        agg.out_of_window += st.out_of_window
+        s += c
+    return agg

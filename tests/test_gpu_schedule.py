@@ -1,0 +1,66 @@
+"""The binned schedule (k > 0 pushes compacted into per-k queues and deferred
+to the next step's kernel) gives exactly the bits of the plain schedule: both
+call the same per-particle arithmetic; only the order of work differs.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import _harness as H
+from paper_2102_10983_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2102_10983_gb300 import native  # noqa: E402
+
+
+def _wl(n, **kw):
+    base = dict(name="sched", n_particles=n, a0=150.0, dt=W.DT75, dx=W.DT75 / 0.99,
+                psi_max=0.01, order=3, n_steps=0, x_lo=0.0, x_hi=8 * math.pi,
+                thermal_sigma=W.MAXWELL_10KEV_SIGMA, seed=4, window=1024, lead=200)
+    base.update(kw)
+    return W.Workload(**base)
+
+
+def _run(wl, schedule, n_steps, call_lens, order=3):
+    integ = native.Integrator(wl.dt, wl.dx, wl.psi_max, order=order, precision=native.PIC_MIXED,
+                              schedule=schedule, capacity=wl.n_particles, window=wl.window,
+                              ring_levels=order + 2 + max(call_lens))
+    ini = wl.particles()
+    integ.pic_particles_write(ini.x, ini.px, ini.py, ini.pz)
+    st = H.run_gpu_calls(integ, wl, order, 0, n_steps, call_lens)
+    out = integ.read_numpy()
+    integ.close()
+    return out, st
+
+
+@pytest.mark.parametrize("call_lens", [[1], [7, 64, 3], [400]])
+@pytest.mark.parametrize("n", [5000, 4097])
+def test_binned_bitwise_equals_plain(call_lens, n):
+    wl = _wl(n)
+    a, sa = _run(wl, native.PIC_SCHED_PLAIN, 1200, call_lens)
+    b, sb = _run(wl, native.PIC_SCHED_BINNED, 1200, call_lens)
+    assert sa.k_hist[5] > 0, "the front must reach the electrons"
+    for u, v in zip(a, b):
+        np.testing.assert_array_equal(u, v)
+    assert list(sa.k_hist) == list(sb.k_hist)
+    assert (sa.substeps, sa.n_star, sa.clamped, sa.out_of_window) == \
+           (sb.substeps, sb.n_star, sb.clamped, sb.out_of_window)
+
+
+@pytest.mark.parametrize("order", [1, 5])
+def test_binned_bitwise_other_orders_and_window_exit(order):
+    wl = _wl(1000, lead=60, window=256)   # a short window: some electrons leave it
+    a, sa = _run(wl, native.PIC_SCHED_PLAIN, 600, [50], order=order)
+    b, sb = _run(wl, native.PIC_SCHED_BINNED, 600, [50], order=order)
+    for u, v in zip(a, b):
+        np.testing.assert_array_equal(u, v)
+    assert sa.out_of_window == sb.out_of_window
+    assert list(sa.k_hist) == list(sb.k_hist)
