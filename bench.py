@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--acc-particles", type=int, default=524288)
     ap.add_argument("--cpu-sample", type=int, default=16384)
     return ap.parse_args()
 
@@ -176,6 +178,68 @@ def device_levels(wl: W.Workload, n_first: int, n_count: int, device):
     return E, B, wl.origins(n_first, n_count)
 
 
+def levels_np_to_device(wl: W.Workload, n_first: int, n_count: int, device):
+    """Seeded host levels (workloads.sample_levels) copied to the device."""
+    import torch
+    E, B, i0 = wl.levels(n_first, n_count)
+    return torch.as_tensor(E, device=device), torch.as_tensor(B, device=device), i0
+
+
+def accuracy_run(wl, ini, n_acc, steps, E, B, i0, ring, stream, dev, sched, sensitivity):
+    """Mixed (binned) vs FP64 (plain) on the first n_acc electrons from step 0.
+    With sensitivity=True a second FP64 run starts from the mixed form's rounded
+    initial state: the spread it shows is the trajectories' own sensitivity."""
+    import torch
+    from paper_2102_10983_gb300 import native
+    p = wl.order
+
+    def run(precision, schedule, init):
+        integ = native.Integrator(wl.dt, wl.dx, wl.psi_max, order=p, precision=precision,
+                                  schedule=schedule, capacity=n_acc, window=wl.window,
+                                  ring_levels=ring, stream=stream)
+        integ.pic_particles_write(*init)
+        for r in range(steps + p):
+            integ.pic_fields_upload(r - p, int(i0[r]), E[r], B[r])
+        integ.pic_push_step(0, steps, want_stats=False)
+        outp = [torch.empty(n_acc, dtype=torch.float64, device=dev) for _ in range(4)]
+        integ.pic_particles_read(*outp)
+        torch.cuda.synchronize()
+        integ.close()
+        return outp
+
+    init = [torch.as_tensor(np.ascontiguousarray(a[:n_acc]), device=dev)
+            for a in (ini.x, ini.px, ini.py, ini.pz)]
+    ref = run(native.PIC_FP64, native.PIC_SCHED_PLAIN, init)
+    mix = run(native.PIC_MIXED, sched, init)
+
+    def cmp(a, b):
+        dpv = torch.stack([(a[q] - b[q]).abs() for q in (1, 2, 3)]).amax(0) / wl.a0 ** 2
+        ga = torch.sqrt(1 + a[1] ** 2 + a[2] ** 2 + a[3] ** 2) - 1
+        gb = torch.sqrt(1 + b[1] ** 2 + b[2] ** 2 + b[3] ** 2) - 1
+        disp = ((a[0] - b[0]).abs() / torch.clamp((a[0] - init[0]).abs(), min=1.0)).max()
+        return {"max_dp_over_a0sq": float(dpv.max()),
+                "frac_dp_over_1e-4": float((dpv > 1e-4).double().mean()),
+                "p99.9_dp_over_a0sq": float(torch.quantile(dpv[:1 << 20].float(), 0.999)),
+                "energy_gain_rel_diff": abs(float(ga.mean() - gb.mean())) / float(ga.mean()),
+                "max_rel_displacement_err": float(disp)}
+
+    res = {"vs": "FP64 GPU form (bit-identical to the FP64 oracle)", "electrons": n_acc,
+           "steps": steps, **cmp(ref, mix)}
+    if sensitivity:
+        # the mixed form's initial rounding, pushed in FP64
+        tmp = native.Integrator(wl.dt, wl.dx, wl.psi_max, order=p, precision=native.PIC_MIXED,
+                                capacity=n_acc, window=wl.window, ring_levels=p + 2, stream=stream)
+        tmp.pic_particles_write(*init)
+        r0 = [torch.empty(n_acc, dtype=torch.float64, device=dev) for _ in range(4)]
+        tmp.pic_particles_read(*r0)
+        torch.cuda.synchronize()
+        tmp.close()
+        ref2 = run(native.PIC_FP64, native.PIC_SCHED_PLAIN, r0)
+        res["fp64_self_sensitivity"] = {
+            "what": "FP64 run from the FP32-rounded initial state vs FP64 run", **cmp(ref, ref2)}
+    return res
+
+
 # ---------------------------------------------------------------- our arm
 
 def run_ours(args, ws, rank, local):
@@ -241,46 +305,49 @@ def run_ours(args, ws, rank, local):
                kern_ms=kern_ms / max(kern_steps, 1), stats=st.as_dict(),
                substeps_per_s=st.substeps * ws / (total_ms / 1e3))
 
-    # ---- accuracy and the FP64 form over the same steps (start .. start+Wu+K64)
+    # ---- the plain FP64 push from the same state (the mixed state at the start of
+    #      the timed window, widened to FP64), K64 steps
     K64 = min(K, args.fp64_steps)
     if not args.no_fp64:
-        acc_end = start + Wu + K64
-        ref = make(native.PIC_FP64, native.PIC_SCHED_PLAIN, last)
-        ref.pic_push_step(0, start + Wu, want_stats=False)
+        mix = make(native.PIC_MIXED, sched, last)
+        mix.pic_push_step(0, start + Wu, want_stats=False)
+        st0 = [torch.empty(n_e, dtype=torch.float64, device=dev) for _ in range(4)]
+        stat0 = torch.empty(n_e, dtype=torch.uint8, device=dev)
+        mix.pic_particles_read(*st0, stat0)
+        mix.close()
+        ref = native.Integrator(wl.dt, wl.dx, wl.psi_max, order=p, precision=native.PIC_FP64,
+                                capacity=n_e, window=wl.window, ring_levels=ring, stream=stream)
+        ref.pic_particles_write(*st0, stat0)
+        for r in range(last + p):
+            ref.pic_fields_upload(r - p, int(i0[r]), E[r], B[r])
         torch.cuda.synchronize()
-        ref.timing(True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         ref.pic_push_step(start + Wu, K64, want_stats=False)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms64 = e0.elapsed_time(e1)
-        ref.timing(False)
-        ms64 = max_over_ranks(ws, ms64)
-        mix = make(native.PIC_MIXED, sched, last)
-        mix.pic_push_step(0, acc_end, want_stats=False)
-        a = [torch.empty(n_e, dtype=torch.float64, device=dev) for _ in range(4)]
-        b = [torch.empty(n_e, dtype=torch.float64, device=dev) for _ in range(4)]
-        ref.pic_particles_read(*a)
-        mix.pic_particles_read(*b)
-        torch.cuda.synchronize()
+        ms64 = max_over_ranks(ws, e0.elapsed_time(e1))
         ref.close()
-        mix.close()
-        x0 = torch.as_tensor(ini.x, device=dev)
-        dpv = torch.stack([(a[q] - b[q]).abs() for q in (1, 2, 3)]).amax(0) / wl.a0 ** 2
-        dp = float(dpv.max())
-        n_out = int((dpv > 1e-4).sum())
-        q9999 = float(torch.quantile(dpv[torch.randperm(n_e, device=dev)[:1 << 20]].float(), 0.9999))
-        ga = torch.sqrt(1 + a[1] ** 2 + a[2] ** 2 + a[3] ** 2) - 1
-        gb = torch.sqrt(1 + b[1] ** 2 + b[2] ** 2 + b[3] ** 2) - 1
-        de = abs(float(ga.mean() - gb.mean())) / float(ga.mean())
-        disp = float(((a[0] - b[0]).abs() / torch.clamp((a[0] - x0).abs(), min=1.0)).max())
+        del st0, stat0
         out.update(fp64_value=n_e * K64 * ws / (ms64 / 1e3), fp64_ms_per_step=ms64 / K64,
-                   fp64_steps=K64,
-                   accuracy={"vs": "FP64 GPU form (bit-identical to the FP64 oracle)",
-                             "at_step": acc_end, "max_dp_over_a0sq": dp,
-                             "electrons_over_1e-4": n_out, "p99.99_dp_over_a0sq": q9999,
-                             "energy_gain_rel_diff": de, "max_rel_displacement_err": disp})
+                   fp64_steps=K64)
+
+    # ---- accuracy of the mixed form against the FP64 form (bit-identical to the
+    #      FP64 oracle) on the first n_acc electrons, steps 0 .. acc_end-1
+    if not args.no_accuracy:
+        n_acc = min(args.acc_particles, n_e)
+        acc_end = start + Wu + K64
+        out["accuracy"] = {
+            "switched_on_front": accuracy_run(wl, ini, n_acc, acc_end, E, B, i0, ring, stream,
+                                              dev, sched, sensitivity=True),
+        }
+        smooth = W.Workload(**{**wl.__dict__, "profile": "gauss", "xi0": 8 * math.pi,
+                               "sigma": 2 * math.pi})
+        Es, Bs, _ = levels_np_to_device(smooth, -p, acc_end + p, dev)
+        out["accuracy"]["smooth_front"] = accuracy_run(smooth, ini, n_acc, acc_end, Es, Bs, i0,
+                                                       ring, stream, dev, sched,
+                                                       sensitivity=False)
+        del Es, Bs
 
     # ---- end to end through the C ABI with host buffers
     if not args.no_e2e:
@@ -396,6 +463,7 @@ def main():
                    "parallelism": f"replicas x{ws}"},
         "substeps_per_s": out["substeps_per_s"],
         "fp64_value": out.get("fp64_value"), "fp64_steps": out.get("fp64_steps"),
+        "fp64_note": "plain FP64 push, same workload and steps, started from the timed window's state",
         "speedup_vs_fp64": (out["value"] / out["fp64_value"]) if out.get("fp64_value") else None,
         "accuracy": out.get("accuracy"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
