@@ -160,9 +160,49 @@ int pic_timing_read(pic_ctx* ctx, double* total_ms, int64_t* steps, int32_t rese
 /* Number of kernel launches the context has queued since creation. */
 int64_t pic_launch_count(const pic_ctx* ctx);
 
-/* Static reason for the last error on this context (or of pic_create when
- * ctx is NULL). */
+/* Static reason for the last error on this context (or of pic_create and
+ * pic_push_mixed_noalloc when ctx is NULL). */
 const char* pic_last_error(const pic_ctx* ctx);
+
+/* Allocation-free variant of the binned mixed-precision push (no counterpart
+ * in the paper: it exists for host programs that may not call cudaMalloc at
+ * push time, e.g. because another framework owns and carves up all device
+ * memory, or because a real-time loop must avoid the allocator).  The caller
+ * owns every input and output; the weight table, per-k queues, work cursor
+ * and counters live in one fixed file-scope __device__ array of ~6.8 MB that
+ * every GPU loading the library holds until the process exits.  Nothing is
+ * allocated: no cudaMalloc/cudaFree, no allocating library call.
+ *
+ *  prm:        as for pic_create; precision must be PIC_MIXED and schedule
+ *              PIC_SCHED_BINNED.
+ *  n_particles <= 65,536 (the size the static queues hold); larger counts are
+ *              rejected with PIC_EINVAL.
+ *  cell, frac, px, py, pz, status: device arrays of n_particles entries in the
+ *              mixed layout (x = (cell + frac) dx, frac in [0, 1); p FP32;
+ *              status byte as in pic_particles_write), updated in place.
+ *  Ey_levels, Bz_levels, level_i0: host arrays of order + n_steps entries;
+ *              entry r describes level n0 - order + r: device pointers to
+ *              window_cells FP32 values of E_y (t = level dt) and B_z
+ *              (t = (level + 1/2) dt), node i stored at index
+ *              i & (window_cells - 1), the window being nodes
+ *              [level_i0[r], level_i0[r] + window_cells).
+ *  n0, n_steps: macro steps n0 .. n0 + n_steps - 1 are taken.
+ *  stream:     cudaStream_t (or NULL); all work is queued on it.
+ *  stats:      optional; if non-NULL the stream is synchronized and the
+ *              counters of this call are returned (PIC_ERANGE / PIC_EKMAX as
+ *              for pic_push_step).
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) and builds the weight table there, so make that first
+ * call before any stream capture.  Every call shares the array and finds the
+ * previous call's contents; the call clears what must start at zero.  Calls
+ * that run concurrently on the GPU (other streams, other host threads) race
+ * on the array and must be serialized by the caller.
+ * Errors: PIC_EINVAL, PIC_ECUDA, PIC_ERANGE, PIC_EKMAX. */
+int pic_push_mixed_noalloc(const pic_params* prm, int64_t n_particles, int32_t* cell,
+                           float* frac, float* px, float* py, float* pz, uint8_t* status,
+                           const float* const* Ey_levels, const float* const* Bz_levels,
+                           const int64_t* level_i0, int64_t window_cells, int64_t n0,
+                           int64_t n_steps, void* stream, pic_step_stats* stats);
 
 #ifdef __cplusplus
 }

@@ -24,6 +24,7 @@ SOURCES = {
     "pic_api.cu": [],
     "push_f64.cu": ["-fmad=false"],
     "push_mixed.cu": [],
+    "push_noalloc.cu": [],
 }
 
 

@@ -48,6 +48,11 @@ struct pic_ctx {
 
 static thread_local char g_create_err[256];
 
+void pic::set_global_error(const char* msg) {
+  strncpy(g_create_err, msg, sizeof(g_create_err) - 1);
+  g_create_err[sizeof(g_create_err) - 1] = 0;
+}
+
 static int fail(pic_ctx* c, int code, const char* fmt, const char* detail = "") {
   char* dst = c ? c->err : g_create_err;
   snprintf(dst, 256, fmt, detail);

@@ -84,6 +84,9 @@ struct PushArgsMixed {
   int finalize;
 };
 
+// Sets the reason pic_last_error(NULL) reports.
+void set_global_error(const char* msg);
+
 // Launchers (return cudaError_t of the launch).
 cudaError_t build_wtab_f64(double* wtab, int order, int k_max, int field_time, cudaStream_t s);
 cudaError_t build_wtab_f32(float* wtab, const double* wtab64, int64_t count, cudaStream_t s);

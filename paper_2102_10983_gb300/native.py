@@ -59,6 +59,9 @@ SIGNATURES = {
     "pic_timing_read": (ctypes.c_int, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_I64), _I32]),
     "pic_launch_count": (ctypes.c_int64, [_VP]),
     "pic_last_error": (ctypes.c_char_p, [_VP]),
+    "pic_push_mixed_noalloc": (ctypes.c_int, [ctypes.POINTER(PicParams), _I64, _VP, _VP, _VP, _VP,
+                                              _VP, _VP, _VP, _VP, _VP, _I64, _I64, _I64, _VP,
+                                              ctypes.POINTER(PicStepStats)]),
 }
 
 _lib = None
