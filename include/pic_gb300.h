@@ -164,6 +164,50 @@ int64_t pic_launch_count(const pic_ctx* ctx);
  * pic_push_mixed_noalloc when ctx is NULL). */
 const char* pic_last_error(const pic_ctx* ctx);
 
+/* ---- learned sub-cycle-count predictor (not in the paper) ----------------
+ * An MLP 6 -> 64 -> 64 -> 8 (ReLU; softmax cross-entropy over k = 0..7) that
+ * predicts the exponent the criterion of Sec. IV will pick at the next macro
+ * step, from phi = (asinh|E_y|, asinh|B_z|, asinh p_x, asinh p_y, asinh p_z,
+ * log gamma).  BF16 tensor-core operands, FP32 accumulation and FP32 master
+ * parameters (packed: W1[64][6] b1[64] W2[64][64] b2[64] W3[8][64] b3[8]).
+ * It never changes a trajectory: the criterion decides every sub-step. */
+
+/* Features of every loaded particle after macro step n (mixed form): E_y and B_z
+ * at the particle extrapolated to t_{n+1} from step n's levels (which must
+ * still be in the ring), and the particle's momentum.  phi: device, n x 6 FP32.
+ * Errors: PIC_EINVAL, PIC_ECUDA. */
+int pic_features(pic_ctx* ctx, int64_t n, float* phi);
+
+typedef struct pic_mlp pic_mlp;
+
+/* Number of packed FP32 parameters (5128). */
+int pic_mlp_param_count(void);
+
+/* Create a predictor (He-uniform weights from `seed`, zero biases) whose work
+ * is queued on `stream`.  Errors: PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA. */
+int pic_mlp_create(uint64_t seed, void* stream, pic_mlp** out);
+
+int pic_mlp_destroy(pic_mlp* mlp);
+
+/* Copy the packed parameters out (set = 0) or in (set = 1; also resets the
+ * optimizer state).  buf holds pic_mlp_param_count() floats in `where` memory. */
+int pic_mlp_params(pic_mlp* mlp, float* buf, int32_t set, int32_t where);
+
+/* Gradient of the mean cross-entropy over n samples (phi: device n x 6 FP32;
+ * label: device n uint8 in 0..7) into grad_out (host, packed) and the loss into
+ * loss_out (host).  Either output may be NULL.  Synchronizes. */
+int pic_mlp_grad(pic_mlp* mlp, const float* phi, const uint8_t* label, int64_t n,
+                 float* grad_out, float* loss_out);
+
+/* One Adam step (beta 0.9 / 0.999) with learning rate lr on the batch; the
+ * batch loss (before the step) goes to loss_out (host) if non-NULL. */
+int pic_mlp_train_step(pic_mlp* mlp, const float* phi, const uint8_t* label, int64_t n,
+                       float lr, float* loss_out);
+
+/* Predicted class (argmax of the logits; ties go to the smaller k) of n
+ * samples: pred is device n uint8.  Asynchronous. */
+int pic_mlp_infer(pic_mlp* mlp, const float* phi, int64_t n, uint8_t* pred);
+
 /* Allocation-free variant of the binned mixed-precision push (no counterpart
  * in the paper: it exists for host programs that may not call cudaMalloc at
  * push time, e.g. because another framework owns and carves up all device

@@ -25,6 +25,8 @@ SOURCES = {
     "push_f64.cu": ["-fmad=false"],
     "push_mixed.cu": [],
     "push_noalloc.cu": [],
+    "mlp_bf16.cu": [],
+    "mlp_api.cu": [],
 }
 
 

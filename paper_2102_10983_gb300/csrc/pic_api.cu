@@ -513,6 +513,7 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
     base.qm_abs = fabsf((float)c->prm.qm);
     base.inv_dx = (float)(1.0 / c->prm.dx);
     base.k_max = c->prm.k_max;
+    base.field_time = c->prm.field_time;
     base.wtab = c->wtab32;
     base.crit_row = wrows_total(c->prm.k_max) - 1;
     base.stats = c->dstats;
@@ -599,5 +600,24 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
     if (c->timing) CUDA_TRY(c, cudaEventRecord(ev1, c->stream));
   }
   if (stats) return collect_stats(c, stats, true);
+  return PIC_OK;
+}
+
+extern "C" int pic_features(pic_ctx* c, int64_t n, float* phi) {
+  if (!c || !phi) return PIC_EINVAL;
+  if (c->prm.precision != PIC_MIXED) return fail(c, PIC_EINVAL, "pic_features: needs the mixed form%s");
+  int slots[kMaxOrder + 1];
+  int64_t lo, hi;
+  int rc = step_slots(c, n, slots, &lo, &hi);
+  if (rc != PIC_OK) return rc;
+  PushArgsMixed a;
+  memset(&a, 0, sizeof(a));
+  a.n = c->n;
+  a.cell = c->cell; a.frac = c->frac; a.px = c->fpx; a.py = c->fpy; a.pz = c->fpz;
+  a.status = c->status;
+  a.mask = (int32_t)(c->W - 1);
+  fill_mixed(c, a, slots, lo, hi, false);
+  CUDA_TRY(c, launch_features_mixed(a, c->prm.order, phi, c->stream));
+  ++c->launches;
   return PIC_OK;
 }

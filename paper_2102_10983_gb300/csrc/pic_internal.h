@@ -69,6 +69,7 @@ struct PushArgsMixed {
   float dt, psi_max, qm, qm_abs;
   float inv_dx;
   int k_max;
+  int field_time;  // 0: theta_j = 1/2 + (j-1)/m; 1: theta_j = (j - 1/2)/m
   const float* wtab;
   int64_t crit_row;
   DevStats* stats;
@@ -93,5 +94,15 @@ cudaError_t build_wtab_f32(float* wtab, const double* wtab64, int64_t count, cud
 cudaError_t launch_push_f64(const PushArgsF64& a, int order, cudaStream_t s, int* launches);
 cudaError_t launch_push_mixed(const PushArgsMixed& a, int order, int schedule, int sm_count,
                               cudaStream_t s, int* launches);
+cudaError_t launch_features_mixed(const PushArgsMixed& a, int order, float* phi, cudaStream_t s);
+
+// predictor (mlp_bf16.cu)
+int mlp_param_count();
+cudaError_t launch_mlp_infer(const float* P, const float* phi, int64_t n, uint8_t* pred,
+                             int sm_count, cudaStream_t s);
+cudaError_t launch_mlp_grad(const float* P, const float* phi, const uint8_t* label, int64_t n,
+                            float* grad, float* loss, int sm_count, cudaStream_t s);
+cudaError_t launch_mlp_adam(float* P, const float* grad, float* m1, float* m2, float lr, int step,
+                            cudaStream_t s);
 
 }  // namespace pic

@@ -33,6 +33,7 @@
 // (the bulk of step j only takes particles whose parity equals j & 1 and flips
 // it), bits 4-6 = deferred k (0 = none), bit 7 = lost.  Outside a call the
 // byte is in the public form (bits 0-6 = k).
+#include <limits.h>
 #include <math.h>
 
 #include "pic_internal.h"
@@ -118,38 +119,128 @@ struct StepFields {
   int32_t lo, hi;
 };
 
+// One Boris sub-step (Eqs. eq:p - eq:gamman) and the position update (Eq. eq:x)
+// in the fields ey, bz, with momentum step hp and offset step hx (cells per
+// unit velocity).
+__device__ __forceinline__ void boris_f32(float ey, float bz, float hp, float hx, float qm,
+                                          MixedState& s) {
+  const float half = __fmul_rn(0.5f, hp);
+  const float dpy = __fmul_rn(__fmul_rn(qm, ey), half);
+  const float mx = s.ux, my = __fadd_rn(s.uy, dpy), mz = s.uz;
+  const float inv_gn = rsqrtf(__fadd_rn(1.0f, norm2(mx, my, mz)));
+  const float tz = __fmul_rn(__fmul_rn(__fmul_rn(qm, bz), half), inv_gn);
+  const float ppx = __fmaf_rn(my, tz, mx);
+  const float ppy = __fmaf_rn(-mx, tz, my);
+  const float sz = __fdividef(__fmul_rn(2.0f, tz), __fmaf_rn(tz, tz, 1.0f));
+  s.ux = __fmaf_rn(ppy, sz, mx);
+  s.uy = __fadd_rn(__fmaf_rn(-ppx, sz, my), dpy);
+  s.uz = mz;
+  const float inv_g = rsqrtf(__fadd_rn(1.0f, norm2(s.ux, s.uy, s.uz)));
+  s.frac = __fmaf_rn(hx, __fmul_rn(s.ux, inv_g), s.frac);
+}
+
+// Reciprocal of prod_{k != j} (j - k), the denominator of L_{p,j} (Sec. VI).
+__host__ __device__ constexpr float lagrange_inv_den(int p, int j) {
+  float d = 1.f;
+  for (int k = 0; k <= p; ++k)
+    if (k != j) d *= (float)(j - k);
+  return 1.f / d;
+}
+
+// Weights of Eqs. eq:lagrange2-3 (E) and eq:lagrange2-2 (B) at theta, in FP32:
+// prod_{k != j} (c_k + theta) times the reciprocal denominator, c_k = p-k-1/2
+// (E) or p-k-1 (B).  Depends on the sub-step index only, so these FP32 ops run
+// alongside the serial chain of the push instead of on it.
+template <int P>
+__device__ __forceinline__ void lagrange_f32(float theta, float* w) {
+#pragma unroll
+  for (int j = 0; j <= P; ++j) {
+    float ne = 1.f, nb = 1.f;
+#pragma unroll
+    for (int k = 0; k <= P; ++k) {
+      if (k == j) continue;
+      ne = __fmul_rn(ne, __fadd_rn((float)(P - k) - 0.5f, theta));
+      nb = __fmul_rn(nb, __fadd_rn((float)(P - k) - 1.0f, theta));
+    }
+    w[j] = __fmul_rn(ne, lagrange_inv_den(P, j));
+    w[P + 1 + j] = __fmul_rn(nb, lagrange_inv_den(P, j));
+  }
+}
+
+// Temporal sum over the levels' values v at one node, then nothing else: the
+// same operation order as gather_f32.
+template <int P>
+__device__ __forceinline__ float tsum(const float* w, const float* v) {
+  float f = __fmul_rn(w[0], v[0]);
+#pragma unroll
+  for (int l = 1; l <= P; ++l) f = __fmaf_rn(w[l], v[l], f);
+  return f;
+}
+
 // The m = 4^k sub-steps of one macro step (Algorithm 1).  False if the particle
 // left the window (state kept as reached).
+//
+// m = 1 takes a straight path with the tabulated weights.  For m > 1 the level
+// values at the two tent nodes of each grid stay in registers while the node
+// index is unchanged (an electron moves a small fraction of a cell per
+// sub-step), and the weights of each sub-step are computed from theta_j on the
+// spot: nothing on the serial chain of a long sub-cycle waits on memory.
 template <int P>
 __device__ __forceinline__ bool subcycle_f32(const StepFields<P>& F, const float* wtab,
                                              int32_t mask, float dt, float inv_dx, float qm,
-                                             int k, int k_prev, MixedState& s) {
+                                             int field_time, int k, int k_prev, MixedState& s) {
   constexpr int stride = 2 * (P + 1);
-  const int m = 1 << (2 * k);
   const float h = ldexpf(dt, -2 * k);
   const float h_old = ldexpf(dt, -2 * k_prev);
   const float hx = __fmul_rn(h, inv_dx);
-  const float* wr = wtab + wrow(k, 1) * stride;
   float hp = __fmul_rn(0.5f, __fadd_rn(h_old, h));
-  for (int j = 1; j <= m; ++j, wr += stride) {
+  if (k == 0) {
+    const float* wr = wtab + wrow(0, 1) * stride;
     int32_t je, jb;
     float we, wb;
     if (!tent_coords(s.cell, s.frac, F.lo, F.hi, je, we, jb, wb)) return false;
     const float ey = gather_f32<P>(F.E, wr, je, we, mask);
     const float bz = gather_f32<P>(F.B, wr + (P + 1), jb, wb, mask);
-    const float half = __fmul_rn(0.5f, hp);
-    const float dpy = __fmul_rn(__fmul_rn(qm, ey), half);
-    const float mx = s.ux, my = __fadd_rn(s.uy, dpy), mz = s.uz;
-    const float inv_gn = rsqrtf(__fadd_rn(1.0f, norm2(mx, my, mz)));
-    const float tz = __fmul_rn(__fmul_rn(__fmul_rn(qm, bz), half), inv_gn);
-    const float ppx = __fmaf_rn(my, tz, mx);
-    const float ppy = __fmaf_rn(-mx, tz, my);
-    const float sz = __fdividef(__fmul_rn(2.0f, tz), __fmaf_rn(tz, tz, 1.0f));
-    s.ux = __fmaf_rn(ppy, sz, mx);
-    s.uy = __fadd_rn(__fmaf_rn(-ppx, sz, my), dpy);
-    s.uz = mz;
-    const float inv_g = rsqrtf(__fadd_rn(1.0f, norm2(s.ux, s.uy, s.uz)));
-    s.frac = __fmaf_rn(hx, __fmul_rn(s.ux, inv_g), s.frac);
+    boris_f32(ey, bz, hp, hx, qm, s);
+    return true;
+  }
+  const int m = 1 << (2 * k);
+  const float inv_m = ldexpf(1.0f, -2 * k);
+  int32_t ce = INT_MIN, cb = INT_MIN;
+  float e0[P + 1], e1[P + 1], b0[P + 1], b1[P + 1];
+  for (int j = 1; j <= m; ++j) {
+    // theta_j = 1/2 + (j-1)/m (position time) or (j - 1/2)/m; exact in FP32 for m <= 4^7
+    const float jm1 = (float)(j - 1);
+    const float theta = field_time == 0 ? __fadd_rn(0.5f, __fmul_rn(jm1, inv_m))
+                                        : __fmul_rn(__fadd_rn(jm1, 0.5f), inv_m);
+    float w[stride];
+    lagrange_f32<P>(theta, w);
+    int32_t je, jb;
+    float we, wb;
+    if (!tent_coords(s.cell, s.frac, F.lo, F.hi, je, we, jb, wb)) return false;
+    if (je != ce) {
+      ce = je;
+      const int32_t a0 = je & mask, a1 = (je + 1) & mask;
+#pragma unroll
+      for (int l = 0; l <= P; ++l) {
+        e0[l] = __ldg(F.E[l] + a0);
+        e1[l] = __ldg(F.E[l] + a1);
+      }
+    }
+    if (jb != cb) {
+      cb = jb;
+      const int32_t a0 = jb & mask, a1 = (jb + 1) & mask;
+#pragma unroll
+      for (int l = 0; l <= P; ++l) {
+        b0[l] = __ldg(F.B[l] + a0);
+        b1[l] = __ldg(F.B[l] + a1);
+      }
+    }
+    const float fe0 = tsum<P>(w, e0), fe1 = tsum<P>(w, e1);
+    const float fb0 = tsum<P>(w + (P + 1), b0), fb1 = tsum<P>(w + (P + 1), b1);
+    const float ey = __fmaf_rn(we, __fsub_rn(fe1, fe0), fe0);
+    const float bz = __fmaf_rn(wb, __fsub_rn(fb1, fb0), fb0);
+    boris_f32(ey, bz, hp, hx, qm, s);
     hp = h;
   }
   return true;
@@ -269,7 +360,7 @@ __global__ void __launch_bounds__(256) push_mixed_plain_kernel(PushArgsMixed a) 
     const int k = criterion_f32<P>(F.B, wcrit, jb, wb, a.mask, s, a.qm_abs, a.dt, a.psi_max,
                                    a.k_max, capped);
     count_step(tc, sh, k, capped);
-    const bool ok = subcycle_f32<P>(F, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, k, st & 0x7f, s);
+    const bool ok = subcycle_f32<P>(F, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, a.field_time, k, st & 0x7f, s);
     normalize(s);
     store_state(a, i, s);
     a.status[i] = ok ? (uint8_t)k : (uint8_t)(k | PIC_STATUS_LOST);
@@ -315,7 +406,7 @@ __device__ __forceinline__ void heavy_particle(const PushArgsMixed& a, const Ste
   const int k = deferred_k(st);
   const int k_prev = st & 7;
   MixedState s = load_state(a, i);
-  const bool ok = subcycle_f32<P>(Fp, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, k, k_prev, s);
+  const bool ok = subcycle_f32<P>(Fp, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, a.field_time, k, k_prev, s);
   normalize(s);
   if (!ok) {
     store_state(a, i, s);
@@ -341,7 +432,7 @@ __device__ __forceinline__ void heavy_particle(const PushArgsMixed& a, const Ste
                                   a.k_max, capped);
   count_step(tc, sh, kn, capped);
   if (kn == 0) {
-    const bool ok2 = subcycle_f32<P>(Fc, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, 0, k, s);
+    const bool ok2 = subcycle_f32<P>(Fc, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, a.field_time, 0, k, s);
     normalize(s);
     store_state(a, i, s);
     a.status[i] = ok2 ? (uint8_t)(a.parity_next ? kParity : 0) : (uint8_t)PIC_STATUS_LOST;
@@ -357,7 +448,17 @@ template <int P>
 __global__ void __launch_bounds__(256) push_mixed_binned_kernel(PushArgsMixed a) {
   __shared__ unsigned long long sh[12];
   __shared__ int s_task[8];
+  __shared__ long long heavy_end[8];  // heavy items: ceil(count/32) per k, largest k first
   if (threadIdx.x < 12) sh[threadIdx.x] = 0ull;
+  if (threadIdx.x == 0) {
+    long long acc = 0;
+    heavy_end[0] = 0;
+    for (int k = 7; k >= 1; --k) {
+      const long long c = (k <= a.k_max) ? a.qcount_in[k] : 0;
+      acc += (c + 31) / 32;
+      heavy_end[k] = acc;
+    }
+  }
   __syncthreads();
   constexpr int stride = 2 * (P + 1);
   const float* wcrit = a.wtab + a.crit_row * stride + (P + 1);
@@ -368,15 +469,7 @@ __global__ void __launch_bounds__(256) push_mixed_binned_kernel(PushArgsMixed a)
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
 
-  // heavy items: ceil(count/32) per k, largest k first
-  int64_t heavy_end[8];
-  int64_t acc = 0;
-  for (int k = 7; k >= 1; --k) {
-    const int64_t c = (k <= a.k_max) ? a.qcount_in[k] : 0;
-    acc += (c + 31) / 32;
-    heavy_end[k] = acc;
-  }
-  const int64_t n_heavy = acc;
+  const int64_t n_heavy = heavy_end[1];
   const int64_t n_bulk = a.finalize ? (a.n + kChunk - 1) / kChunk : (a.n + kChunk - 1) / kChunk;
   const int64_t n_items = n_heavy + n_bulk;
 
@@ -467,8 +560,8 @@ __global__ void __launch_bounds__(256) push_mixed_binned_kernel(PushArgsMixed a)
           count_step(tc, sh, k, capped);
           const int k_prev = st[v] & 7;
           if (k == 0) {
-            const bool ok = subcycle_f32<P>(Fc, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, 0, k_prev,
-                                            s[v]);
+            const bool ok = subcycle_f32<P>(Fc, a.wtab, a.mask, a.dt, a.inv_dx, a.qm,
+                                            a.field_time, 0, k_prev, s[v]);
             normalize(s[v]);
             st[v] = ok ? (uint8_t)(a.parity_next ? kParity : 0) : (uint8_t)PIC_STATUS_LOST;
             if (!ok) atomicAdd(&sh[11], 1ull);
@@ -513,6 +606,57 @@ __global__ void __launch_bounds__(256) push_mixed_binned_kernel(PushArgsMixed a)
       __threadfence();
     }
   }
+}
+
+// ---------------------------------------------------------------- predictor features
+
+// phi = (asinh|E|, asinh|B|, asinh p_x, asinh p_y, asinh p_z, log gamma) of each
+// particle after macro step n, with E and B at its position extrapolated to
+// t_{n+1} (theta = 3/2) from step n's levels: everything known before level
+// n+1 arrives.  Lost particles get zeros.
+template <int P>
+__global__ void features_kernel(PushArgsMixed a, float* phi) {
+  StepFields<P> F;
+  load_fields<P>(F, a.E, a.B, a.lo, a.hi);
+  float w[2 * (P + 1)];
+  lagrange_f32<P>(1.5f, w);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const uint8_t st = a.status[i];
+    if (!(st & PIC_STATUS_LOST)) {
+      const MixedState s = load_state(a, i);
+      int32_t je, jb;
+      float we, wb;
+      if (tent_coords(s.cell, s.frac, F.lo, F.hi, je, we, jb, wb)) {
+        const float ey = gather_f32<P>(F.E, w, je, we, a.mask);
+        const float bz = gather_f32<P>(F.B, w + (P + 1), jb, wb, a.mask);
+        f[0] = asinhf(fabsf(ey));
+        f[1] = asinhf(fabsf(bz));
+      }
+      f[2] = asinhf(s.ux);
+      f[3] = asinhf(s.uy);
+      f[4] = asinhf(s.uz);
+      f[5] = 0.5f * log1pf(norm2(s.ux, s.uy, s.uz));
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q) phi[i * 6 + q] = f[q];
+  }
+}
+
+cudaError_t launch_features_mixed(const PushArgsMixed& a, int order, float* phi, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  const int64_t want = (a.n + 255) / 256;
+  const int blocks = (int)(want < 152 * 16 ? want : 152 * 16);
+  switch (order) {
+    case 1: features_kernel<1><<<blocks, 256, 0, s>>>(a, phi); break;
+    case 2: features_kernel<2><<<blocks, 256, 0, s>>>(a, phi); break;
+    case 3: features_kernel<3><<<blocks, 256, 0, s>>>(a, phi); break;
+    case 4: features_kernel<4><<<blocks, 256, 0, s>>>(a, phi); break;
+    case 5: features_kernel<5><<<blocks, 256, 0, s>>>(a, phi); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- launch

@@ -152,6 +152,7 @@ extern "C" int pic_push_mixed_noalloc(const pic_params* prm, int64_t n_particles
   base.qm_abs = fabsf((float)prm->qm);
   base.inv_dx = (float)(1.0 / prm->dx);
   base.k_max = prm->k_max;
+  base.field_time = prm->field_time;
   base.wtab = S->wtab32;
   base.crit_row = wrows_total(prm->k_max) - 1;
   base.stats = &S->stats;

@@ -59,6 +59,14 @@ SIGNATURES = {
     "pic_timing_read": (ctypes.c_int, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_I64), _I32]),
     "pic_launch_count": (ctypes.c_int64, [_VP]),
     "pic_last_error": (ctypes.c_char_p, [_VP]),
+    "pic_features": (ctypes.c_int, [_VP, _I64, _VP]),
+    "pic_mlp_param_count": (ctypes.c_int, []),
+    "pic_mlp_create": (ctypes.c_int, [ctypes.c_uint64, _VP, ctypes.POINTER(_VP)]),
+    "pic_mlp_destroy": (ctypes.c_int, [_VP]),
+    "pic_mlp_params": (ctypes.c_int, [_VP, _VP, _I32, _I32]),
+    "pic_mlp_grad": (ctypes.c_int, [_VP, _VP, _VP, _I64, _VP, _VP]),
+    "pic_mlp_train_step": (ctypes.c_int, [_VP, _VP, _VP, _I64, ctypes.c_float, _VP]),
+    "pic_mlp_infer": (ctypes.c_int, [_VP, _VP, _I64, _VP]),
     "pic_push_mixed_noalloc": (ctypes.c_int, [ctypes.POINTER(PicParams), _I64, _VP, _VP, _VP, _VP,
                                               _VP, _VP, _VP, _VP, _VP, _I64, _I64, _I64, _VP,
                                               ctypes.POINTER(PicStepStats)]),
@@ -211,3 +219,72 @@ class Integrator:
         out = [np.empty(n) for _ in range(4)] + [np.empty(n, np.uint8)]
         self.pic_particles_read(*out)
         return out
+
+
+class Predictor:
+    """The learned sub-cycle-count predictor (pic_mlp_*): device tensors in and out."""
+
+    def __init__(self, seed: int = 0, stream=None):
+        h = ctypes.c_void_p()
+        _check(lib().pic_mlp_create(int(seed), _stream_handle(stream), ctypes.byref(h)))
+        self.h = h
+        self.n_params = int(lib().pic_mlp_param_count())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pic_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        buf = np.empty(self.n_params, dtype=np.float32)
+        _check(lib().pic_mlp_params(self.h, buf.ctypes.data, 0, PIC_HOST))
+        return buf
+
+    def set_params(self, buf):
+        buf = np.ascontiguousarray(buf, dtype=np.float32)
+        assert buf.shape == (self.n_params,)
+        _check(lib().pic_mlp_params(self.h, buf.ctypes.data, 1, PIC_HOST))
+
+    def grad(self, phi, label):
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(lib().pic_mlp_grad(self.h, phi.data_ptr(), label.data_ptr(), int(phi.shape[0]),
+                                  g.ctypes.data, ctypes.byref(loss)))
+        return g, float(loss.value)
+
+    def train_step(self, phi, label, lr: float) -> float:
+        loss = ctypes.c_float()
+        _check(lib().pic_mlp_train_step(self.h, phi.data_ptr(), label.data_ptr(),
+                                        int(phi.shape[0]), float(lr), ctypes.byref(loss)))
+        return float(loss.value)
+
+    def infer(self, phi, pred):
+        _check(lib().pic_mlp_infer(self.h, phi.data_ptr(), int(phi.shape[0]), pred.data_ptr()))
+
+
+def features(integ: "Integrator", n: int, phi):
+    """pic_features: predictor inputs of every particle after macro step n."""
+    _check(lib().pic_features(integ.ctx, int(n), phi.data_ptr()), integ.ctx)
+
+
+def pack_params(P: dict) -> np.ndarray:
+    """Oracle-style parameter dict -> the packed FP32 layout of pic_mlp_params."""
+    return np.concatenate([np.asarray(P[k], dtype=np.float64).reshape(-1)
+                           for k in ("W1", "b1", "W2", "b2", "W3", "b3")]).astype(np.float32)
+
+
+def unpack_params(buf) -> dict:
+    buf = np.asarray(buf, dtype=np.float64)
+    out, off = {}, 0
+    for name, shape in (("W1", (64, 6)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)),
+                        ("W3", (8, 64)), ("b3", (8,))):
+        size = int(np.prod(shape))
+        out[name] = buf[off:off + size].reshape(shape)
+        off += size
+    return out
