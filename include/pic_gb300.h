@@ -64,6 +64,10 @@ extern "C" {
 #define PIC_SCHED_BINNED 1  /* m = 1 particles streamed; k > 0 particles compacted
                                by warp ballot into per-k queues and drained by
                                warps of equal k                                   */
+#define PIC_SCHED_PREDICTED 2 /* binned, and before each launch the particles an
+                                 attached predictor (pic_attach_predictor) expects
+                                 to sub-cycle are binned by predicted k and pushed
+                                 first; the criterion still decides every k      */
 
 /* per-particle status byte: low 7 bits = k of the last macro step; bit 7 set =
    the particle left the field window and is frozen */
@@ -179,6 +183,13 @@ const char* pic_last_error(const pic_ctx* ctx);
 int pic_features(pic_ctx* ctx, int64_t n, float* phi);
 
 typedef struct pic_mlp pic_mlp;
+
+/* Attach a predictor to a PIC_SCHED_PREDICTED context: every `every` steps of
+ * pic_push_step, the features after the previous step go through the network
+ * and its predicted k bins the particles before the next launch (predictions
+ * are reused in between).  The predictor must outlive its use by the context.
+ * Errors: PIC_EINVAL. */
+int pic_attach_predictor(pic_ctx* ctx, pic_mlp* mlp, int32_t every);
 
 /* Number of packed FP32 parameters (5128). */
 int pic_mlp_param_count(void);

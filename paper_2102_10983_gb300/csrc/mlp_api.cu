@@ -158,3 +158,5 @@ extern "C" int pic_mlp_infer(pic_mlp* m, const float* phi, int64_t n, uint8_t* p
   MLP_TRY(launch_mlp_infer(m->P, phi, n, pred, m->sm_count, m->stream));
   return PIC_OK;
 }
+
+const float* pic::mlp_device_params(const pic_mlp* m) { return m ? m->P : nullptr; }

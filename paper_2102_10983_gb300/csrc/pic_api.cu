@@ -37,7 +37,14 @@ struct pic_ctx {
   DevStats* dstats = nullptr;
   // binned schedule scratch
   int32_t* queue = nullptr;
-  int32_t* qcount = nullptr;
+  int32_t* qcount = nullptr;  // [0,16) deferred counts, 16 cursor, 18 blocks done, [32,40) predicted counts
+  // predicted schedule
+  uint8_t* pred = nullptr;
+  float* phi = nullptr;
+  int32_t* pred_queue = nullptr;
+  const pic_mlp* mlp = nullptr;
+  int32_t predict_every = 1;
+
   int64_t launches = 0;
   // optional CUDA-event timing of push steps
   bool timing = false;
@@ -75,9 +82,10 @@ static void free_events(pic_ctx* c) {
 
 static void free_all(pic_ctx* c) {
   free_events(c);
+
   void* ptrs[] = {c->x, c->px, c->py, c->pz, c->cell, c->frac, c->fpx, c->fpy, c->fpz,
                   c->status, c->ringE, c->ringB, c->staging, c->wtab64, c->wtab32,
-                  c->dstats, c->queue, c->qcount};
+                  c->dstats, c->queue, c->qcount, c->pred, c->phi, c->pred_queue};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -152,17 +160,18 @@ extern "C" int pic_create(const pic_params* prm, int64_t capacity, int64_t windo
     return fail(nullptr, PIC_EINVAL, "pic_create: precision must be PIC_FP64 or PIC_MIXED%s");
   if (prm->field_time != 0 && prm->field_time != 1)
     return fail(nullptr, PIC_EINVAL, "pic_create: field_time must be 0 or 1%s");
-  if (prm->schedule != PIC_SCHED_PLAIN && prm->schedule != PIC_SCHED_BINNED)
+  if (prm->schedule != PIC_SCHED_PLAIN && prm->schedule != PIC_SCHED_BINNED &&
+      prm->schedule != PIC_SCHED_PREDICTED)
     return fail(nullptr, PIC_EINVAL, "pic_create: unknown schedule%s");
-  if (prm->schedule == PIC_SCHED_BINNED && prm->precision != PIC_MIXED)
-    return fail(nullptr, PIC_EINVAL, "pic_create: the binned schedule needs PIC_MIXED%s");
+  if (prm->schedule != PIC_SCHED_PLAIN && prm->precision != PIC_MIXED)
+    return fail(nullptr, PIC_EINVAL, "pic_create: the binned schedules need PIC_MIXED%s");
   if (capacity < 0 || capacity > ((int64_t)1 << 31) - 1)
     return fail(nullptr, PIC_EINVAL, "pic_create: capacity must be 0..2^31-1%s");
   if (!is_pow2(window_cells) || window_cells < 16 || window_cells > ((int64_t)1 << 30))
     return fail(nullptr, PIC_EINVAL, "pic_create: window_cells must be a power of two >= 16%s");
   if (ring_levels < prm->order + 1 || ring_levels > (1 << 20))
     return fail(nullptr, PIC_EINVAL, "pic_create: ring_levels must be >= order + 1%s");
-  if (prm->schedule == PIC_SCHED_BINNED && ring_levels < prm->order + 2)
+  if (prm->schedule != PIC_SCHED_PLAIN && ring_levels < prm->order + 2)
     return fail(nullptr, PIC_EINVAL, "pic_create: the binned schedule needs ring_levels >= order + 2%s");
 
   pic_ctx* c = new (std::nothrow) pic_ctx();
@@ -191,9 +200,14 @@ extern "C" int pic_create(const pic_params* prm, int64_t capacity, int64_t windo
     A((void**)&c->fpx, cap * 4);
     A((void**)&c->fpy, cap * 4);
     A((void**)&c->fpz, cap * 4);
-    if (prm->schedule == PIC_SCHED_BINNED) {
+    if (prm->schedule != PIC_SCHED_PLAIN) {
       A((void**)&c->queue, 2 * 7 * cap * 4);
       A((void**)&c->qcount, 64 * 4);
+    }
+    if (prm->schedule == PIC_SCHED_PREDICTED) {
+      A((void**)&c->pred, cap);
+      A((void**)&c->phi, cap * 6 * sizeof(float));
+      A((void**)&c->pred_queue, 7 * cap * 4);
     }
   } else {
     A((void**)&c->x, cap * 8);
@@ -221,6 +235,8 @@ extern "C" int pic_create(const pic_params* prm, int64_t capacity, int64_t windo
   }
   e = cudaMemsetAsync(c->dstats, 0, sizeof(DevStats), c->stream);
   if (e == cudaSuccess && c->qcount) e = cudaMemsetAsync(c->qcount, 0, 64 * 4, c->stream);
+  if (e == cudaSuccess && c->pred) e = cudaMemsetAsync(c->pred, 0, cap, c->stream);
+
   if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, cap, c->stream);
   if (e == cudaSuccess) e = build_wtab_f64(c->wtab64, prm->order, prm->k_max, prm->field_time, c->stream);
   if (e == cudaSuccess) ++c->launches;
@@ -490,7 +506,8 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
   if (n_steps < 1) return fail(c, PIC_EINVAL, "pic_push_step: n_steps must be >= 1%s");
   const int p = c->prm.order;
   const int64_t W = c->W;
-  const bool binned = c->prm.schedule == PIC_SCHED_BINNED;
+  const bool binned = c->prm.schedule != PIC_SCHED_PLAIN;
+  const bool predicted = c->prm.schedule == PIC_SCHED_PREDICTED && c->mlp != nullptr;
   // validate every step's levels before queuing anything
   for (int64_t s = n; s < n + n_steps; ++s) {
     int slots[kMaxOrder + 1];
@@ -514,13 +531,14 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
     base.inv_dx = (float)(1.0 / c->prm.dx);
     base.k_max = c->prm.k_max;
     base.field_time = c->prm.field_time;
+    lagrange_monomials(c->prm.order, base.mono);
     base.wtab = c->wtab32;
     base.crit_row = wrows_total(c->prm.k_max) - 1;
     base.stats = c->dstats;
     base.qcap = c->capacity;
     if (binned) {
       base.cursor = (int*)(c->qcount + 16);
-      base.blocks_done = (unsigned*)(c->qcount + 17);
+      base.blocks_done = (unsigned*)(c->qcount + 18);
     }
   }
   for (int64_t j = 0; j < n_steps; ++j) {
@@ -579,7 +597,29 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
         a.parity_cur = (int)(j & 1);
         a.parity_next = (int)((j + 1) & 1);
         a.finalize = 0;
-        e = launch_push_mixed(a, p, c->prm.schedule, c->sm_count, c->stream, &launches);
+        e = cudaSuccess;
+        if (predicted) {
+          // refresh the predictions from the state after the previous step
+          int ps[kMaxOrder + 1];
+          int64_t plo, phi;
+          if (j % c->predict_every == 0 && step_slots(c, s - 1, ps, &plo, &phi) == PIC_OK) {
+            PushArgsMixed fa = a;
+            fill_mixed(c, fa, ps, plo, phi, false);
+            e = launch_features_mixed(fa, p, c->phi, c->stream);
+            if (e == cudaSuccess)
+              e = launch_mlp_infer(mlp_device_params(c->mlp), c->phi, c->n, c->pred, c->sm_count,
+                                   c->stream);
+            launches += 2;
+          }
+          if (e == cudaSuccess)
+            e = launch_bin_predicted(c->pred, c->status, c->n, a.parity_cur, c->pred_queue,
+                                     c->qcount + 32, c->capacity, c->stream);
+          ++launches;
+          a.pred_queue = c->pred_queue;
+          a.pred_count = c->qcount + 32;
+        }
+        if (e == cudaSuccess)
+          e = launch_binned_step(a, p, c->sm_count, c->stream, &launches);
         if (e == cudaSuccess && j == n_steps - 1) {
           // close the call: finish what the last step deferred, public status bytes
           PushArgsMixed f = a;
@@ -589,7 +629,9 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
           f.queue_out = c->queue + ((n_steps + 1) & 1) * qsz;
           f.qcount_out = c->qcount + ((n_steps + 1) & 1) * 8;
           f.finalize = 1;
-          e = launch_push_mixed(f, p, c->prm.schedule, c->sm_count, c->stream, &launches);
+          f.pred_queue = nullptr;
+          f.pred_count = nullptr;
+          e = launch_binned_step(f, p, c->sm_count, c->stream, &launches);
         }
       } else {
         e = launch_push_mixed(a, p, c->prm.schedule, c->sm_count, c->stream, &launches);
@@ -619,5 +661,15 @@ extern "C" int pic_features(pic_ctx* c, int64_t n, float* phi) {
   fill_mixed(c, a, slots, lo, hi, false);
   CUDA_TRY(c, launch_features_mixed(a, c->prm.order, phi, c->stream));
   ++c->launches;
+  return PIC_OK;
+}
+
+extern "C" int pic_attach_predictor(pic_ctx* c, pic_mlp* mlp, int32_t every) {
+  if (!c) return PIC_EINVAL;
+  if (c->prm.schedule != PIC_SCHED_PREDICTED)
+    return fail(c, PIC_EINVAL, "pic_attach_predictor: the context's schedule is not PIC_SCHED_PREDICTED%s");
+  if (every < 1) return fail(c, PIC_EINVAL, "pic_attach_predictor: every must be >= 1%s");
+  c->mlp = mlp;
+  c->predict_every = every;
   return PIC_OK;
 }

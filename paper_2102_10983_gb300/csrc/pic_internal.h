@@ -70,6 +70,9 @@ struct PushArgsMixed {
   float inv_dx;
   int k_max;
   int field_time;  // 0: theta_j = 1/2 + (j-1)/m; 1: theta_j = (j - 1/2)/m
+  // monomial coefficients, in u = theta - 1, of the Lagrange basis polynomials:
+  // L^E_{p,l}(theta) = sum_q mono[0][l][q] u^q, L^B likewise with mono[1]
+  float mono[2][kMaxOrder + 1][kMaxOrder + 1];
   const float* wtab;
   int64_t crit_row;
   DevStats* stats;
@@ -79,11 +82,18 @@ struct PushArgsMixed {
   int32_t* qcount_in;   // [8], consumed by this launch, zeroed by its last block
   int32_t* qcount_out;  // [8], filled by this launch
   int64_t qcap;
-  int* cursor;
-  unsigned* blocks_done;
+  int* cursor;            // work cursor of the launch
+  unsigned* blocks_done;  // blocks finished
   int parity_cur, parity_next;
   int finalize;
+  // predicted schedule: electrons binned before the launch by predicted k
+  // (per-k queues, qcap entries each), pushed by this launch in full
+  const int32_t* pred_queue;
+  int32_t* pred_count;  // [8], zeroed by this launch's last block
 };
+
+// Fills PushArgsMixed::mono for order p (host side, FP64 expansion).
+void lagrange_monomials(int p, float (&mono)[2][kMaxOrder + 1][kMaxOrder + 1]);
 
 // Sets the reason pic_last_error(NULL) reports.
 void set_global_error(const char* msg);
@@ -94,9 +104,18 @@ cudaError_t build_wtab_f32(float* wtab, const double* wtab64, int64_t count, cud
 cudaError_t launch_push_f64(const PushArgsF64& a, int order, cudaStream_t s, int* launches);
 cudaError_t launch_push_mixed(const PushArgsMixed& a, int order, int schedule, int sm_count,
                               cudaStream_t s, int* launches);
+// One binned step (one launch); with a.finalize set, the closing launch of a
+// call (the last step's deferred particles, then public status bytes).
+cudaError_t launch_binned_step(const PushArgsMixed& a, int order, int sm_count, cudaStream_t main,
+                               int* launches);
 cudaError_t launch_features_mixed(const PushArgsMixed& a, int order, float* phi, cudaStream_t s);
 
-// predictor (mlp_bf16.cu)
+cudaError_t launch_bin_predicted(const uint8_t* pred, uint8_t* status, int64_t n, int parity_cur,
+                                 int32_t* pred_queue, int32_t* pred_count, int64_t qcap,
+                                 cudaStream_t s);
+
+// predictor (mlp_bf16.cu, mlp_api.cu)
+const float* mlp_device_params(const struct ::pic_mlp* m);
 int mlp_param_count();
 cudaError_t launch_mlp_infer(const float* P, const float* phi, int64_t n, uint8_t* pred,
                              int sm_count, cudaStream_t s);

@@ -94,12 +94,8 @@ __device__ __forceinline__ float norm2(float a, float b, float c) {
 
 // Criterion (Sec. IV) in FP32: Psi0 = |q/m| |B| dt / (2 gamma); smallest k with
 // Psi0 / 4^k <= Psi_max, capped at k_max.
-template <int P>
-__device__ __forceinline__ int criterion_f32(const float* const* B, const float* wcrit, int32_t jb,
-                                             float wb, int32_t mask, const MixedState& s,
-                                             float qm_abs, float dt, float psi_max, int k_max,
-                                             bool& capped) {
-  const float b0 = gather_f32<P>(B, wcrit, jb, wb, mask);
+__device__ __forceinline__ int psi_to_k(float b0, const MixedState& s, float qm_abs, float dt,
+                                        float psi_max, int k_max, bool& capped) {
   const float g0 = __fsqrt_rn(__fadd_rn(1.0f, norm2(s.ux, s.uy, s.uz)));
   float psi = __fdiv_rn(__fmul_rn(__fmul_rn(qm_abs, fabsf(b0)), dt), __fmul_rn(2.0f, g0));
   int k = 0;
@@ -109,6 +105,17 @@ __device__ __forceinline__ int criterion_f32(const float* const* B, const float*
   }
   capped = psi > psi_max;
   return k;
+}
+
+// b0 is B_z at the particle and t_n: with m = 1 it is also the first (and only)
+// sub-step's B_z, since both use the theta = 1/2 weights at the same nodes.
+template <int P>
+__device__ __forceinline__ int criterion_f32(const float* const* B, const float* wcrit, int32_t jb,
+                                             float wb, int32_t mask, const MixedState& s,
+                                             float qm_abs, float dt, float psi_max, int k_max,
+                                             bool& capped, float& b0) {
+  b0 = gather_f32<P>(B, wcrit, jb, wb, mask);
+  return psi_to_k(b0, s, qm_abs, dt, psi_max, k_max, capped);
 }
 
 // Field view of one macro step.
@@ -167,6 +174,31 @@ __device__ __forceinline__ void lagrange_f32(float theta, float* w) {
   }
 }
 
+// Lagrange basis polynomials of Sec. VI in monomial form around theta = 1:
+// the nodes in u = theta - 1 are l - p - 1/2 (E) and l - p (B); multiply out
+// prod_{k != l} (u - u_k) / (u_l - u_k) in FP64.
+void lagrange_monomials(int p, float (&mono)[2][kMaxOrder + 1][kMaxOrder + 1]) {
+  for (int grid = 0; grid < 2; ++grid) {
+    const double off = grid == 0 ? -0.5 : 0.0;
+    for (int l = 0; l <= kMaxOrder; ++l)
+      for (int q = 0; q <= kMaxOrder; ++q) mono[grid][l][q] = 0.f;
+    for (int l = 0; l <= p; ++l) {
+      double c[kMaxOrder + 2] = {1.0};
+      int deg = 0;
+      double den = 1.0;
+      const double ul = (double)(l - p) + off;
+      for (int k = 0; k <= p; ++k) {
+        if (k == l) continue;
+        const double uk = (double)(k - p) + off;
+        for (int q = deg + 1; q >= 0; --q) c[q] = (q > 0 ? c[q - 1] : 0.0) - uk * c[q];
+        ++deg;
+        den *= ul - uk;
+      }
+      for (int q = 0; q <= p; ++q) mono[grid][l][q] = (float)(c[q] / den);
+    }
+  }
+}
+
 // Temporal sum over the levels' values v at one node, then nothing else: the
 // same operation order as gather_f32.
 template <int P>
@@ -180,15 +212,51 @@ __device__ __forceinline__ float tsum(const float* w, const float* v) {
 // The m = 4^k sub-steps of one macro step (Algorithm 1).  False if the particle
 // left the window (state kept as reached).
 //
-// m = 1 takes a straight path with the tabulated weights.  For m > 1 the level
-// values at the two tent nodes of each grid stay in registers while the node
-// index is unchanged (an electron moves a small fraction of a cell per
-// sub-step), and the weights of each sub-step are computed from theta_j on the
-// spot: nothing on the serial chain of a long sub-cycle waits on memory.
+// Coefficients of the interpolating polynomial in u at two nodes a0, a1 of the
+// given levels: c_q = sum_l v_l M[l][q].
+template <int P>
+__device__ __forceinline__ void to_monomial(const float* const* lv, int32_t a0, int32_t a1,
+                                            const float (&M)[kMaxOrder + 1][kMaxOrder + 1],
+                                            float* c0, float* c1) {
+  float v0[P + 1], v1[P + 1];
+#pragma unroll
+  for (int l = 0; l <= P; ++l) {
+    v0[l] = __ldg(lv[l] + a0);
+    v1[l] = __ldg(lv[l] + a1);
+  }
+#pragma unroll
+  for (int q = 0; q <= P; ++q) {
+    float x0 = __fmul_rn(v0[0], M[0][q]), x1 = __fmul_rn(v1[0], M[0][q]);
+#pragma unroll
+    for (int l = 1; l <= P; ++l) {
+      x0 = __fmaf_rn(v0[l], M[l][q], x0);
+      x1 = __fmaf_rn(v1[l], M[l][q], x1);
+    }
+    c0[q] = x0;
+    c1[q] = x1;
+  }
+}
+
+template <int P>
+__device__ __forceinline__ float horner(const float* c, float u) {
+  float f = c[P];
+#pragma unroll
+  for (int q = P - 1; q >= 0; --q) f = __fmaf_rn(f, u, c[q]);
+  return f;
+}
+
+// m = 1 takes a straight path with the tabulated weights and the criterion's
+// B_z (b0; unused for m > 1).  For m > 1 the
+// temporal interpolant at each tent node is a polynomial of degree p in
+// u = theta - 1; its coefficients are formed when the node index changes (an
+// electron moves a small fraction of a cell per sub-step) and each sub-step
+// evaluates it by Horner's rule: p FMAs per node, nothing waits on memory.
 template <int P>
 __device__ __forceinline__ bool subcycle_f32(const StepFields<P>& F, const float* wtab,
                                              int32_t mask, float dt, float inv_dx, float qm,
-                                             int field_time, int k, int k_prev, MixedState& s) {
+                                             int field_time,
+                                             const float (&mono)[2][kMaxOrder + 1][kMaxOrder + 1],
+                                             int k, int k_prev, float b0, MixedState& s) {
   constexpr int stride = 2 * (P + 1);
   const float h = ldexpf(dt, -2 * k);
   const float h_old = ldexpf(dt, -2 * k_prev);
@@ -200,44 +268,30 @@ __device__ __forceinline__ bool subcycle_f32(const StepFields<P>& F, const float
     float we, wb;
     if (!tent_coords(s.cell, s.frac, F.lo, F.hi, je, we, jb, wb)) return false;
     const float ey = gather_f32<P>(F.E, wr, je, we, mask);
-    const float bz = gather_f32<P>(F.B, wr + (P + 1), jb, wb, mask);
-    boris_f32(ey, bz, hp, hx, qm, s);
+    boris_f32(ey, b0, hp, hx, qm, s);  // b0: the criterion's B_z (same weights, same nodes)
     return true;
   }
   const int m = 1 << (2 * k);
   const float inv_m = ldexpf(1.0f, -2 * k);
+  // u_j = theta_j - 1, exact in FP32 for m <= 4^7
+  const float u1 = field_time == 0 ? -0.5f : __fsub_rn(__fmul_rn(0.5f, inv_m), 1.0f);
   int32_t ce = INT_MIN, cb = INT_MIN;
-  float e0[P + 1], e1[P + 1], b0[P + 1], b1[P + 1];
+  float ce0[P + 1], ce1[P + 1], cb0[P + 1], cb1[P + 1];  // monomial coefficients per node
   for (int j = 1; j <= m; ++j) {
-    // theta_j = 1/2 + (j-1)/m (position time) or (j - 1/2)/m; exact in FP32 for m <= 4^7
-    const float jm1 = (float)(j - 1);
-    const float theta = field_time == 0 ? __fadd_rn(0.5f, __fmul_rn(jm1, inv_m))
-                                        : __fmul_rn(__fadd_rn(jm1, 0.5f), inv_m);
-    float w[stride];
-    lagrange_f32<P>(theta, w);
+    const float u = __fmaf_rn((float)(j - 1), inv_m, u1);
     int32_t je, jb;
     float we, wb;
     if (!tent_coords(s.cell, s.frac, F.lo, F.hi, je, we, jb, wb)) return false;
     if (je != ce) {
       ce = je;
-      const int32_t a0 = je & mask, a1 = (je + 1) & mask;
-#pragma unroll
-      for (int l = 0; l <= P; ++l) {
-        e0[l] = __ldg(F.E[l] + a0);
-        e1[l] = __ldg(F.E[l] + a1);
-      }
+      to_monomial<P>(F.E, je & mask, (je + 1) & mask, mono[0], ce0, ce1);
     }
     if (jb != cb) {
       cb = jb;
-      const int32_t a0 = jb & mask, a1 = (jb + 1) & mask;
-#pragma unroll
-      for (int l = 0; l <= P; ++l) {
-        b0[l] = __ldg(F.B[l] + a0);
-        b1[l] = __ldg(F.B[l] + a1);
-      }
+      to_monomial<P>(F.B, jb & mask, (jb + 1) & mask, mono[1], cb0, cb1);
     }
-    const float fe0 = tsum<P>(w, e0), fe1 = tsum<P>(w, e1);
-    const float fb0 = tsum<P>(w + (P + 1), b0), fb1 = tsum<P>(w + (P + 1), b1);
+    const float fe0 = horner<P>(ce0, u), fe1 = horner<P>(ce1, u);
+    const float fb0 = horner<P>(cb0, u), fb1 = horner<P>(cb1, u);
     const float ey = __fmaf_rn(we, __fsub_rn(fe1, fe0), fe0);
     const float bz = __fmaf_rn(wb, __fsub_rn(fb1, fb0), fb0);
     boris_f32(ey, bz, hp, hx, qm, s);
@@ -357,10 +411,12 @@ __global__ void __launch_bounds__(256) push_mixed_plain_kernel(PushArgsMixed a) 
       continue;
     }
     bool capped;
+    float b0;
     const int k = criterion_f32<P>(F.B, wcrit, jb, wb, a.mask, s, a.qm_abs, a.dt, a.psi_max,
-                                   a.k_max, capped);
+                                   a.k_max, capped, b0);
     count_step(tc, sh, k, capped);
-    const bool ok = subcycle_f32<P>(F, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, a.field_time, k, st & 0x7f, s);
+    const bool ok = subcycle_f32<P>(F, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, a.field_time, a.mono,
+                                    k, st & 0x7f, b0, s);
     normalize(s);
     store_state(a, i, s);
     a.status[i] = ok ? (uint8_t)k : (uint8_t)(k | PIC_STATUS_LOST);
@@ -370,16 +426,40 @@ __global__ void __launch_bounds__(256) push_mixed_plain_kernel(PushArgsMixed a) 
 }
 
 // ---------------------------------------------------------------- BINNED schedule
+//
+// One persistent kernel per macro step; every warp takes work items from one
+// atomic cursor, in this order:
+//  1. deferred items (k >= kDeferMin, largest k first, 32 particles each): the
+//     particles whose criterion picked a long sub-cycle in the previous step.
+//     Each finishes that step, then takes its criterion for this one (pushed at
+//     once unless k >= kDeferMin again).  Being first, the longest serial
+//     chains start as the launch starts and run beside the stream below.
+//  2. predicted items (predicted schedule only): particles binned before the
+//     launch by the predictor's k, pushed fully, largest k first.
+//  3. stream chunks of kChunk particles, one per thread, the next particle's
+//     state loaded while the current one is pushed.  k = 0: pushed at once (the
+//     criterion's B_z serves the push).  k = 1, 2: parked in the warp's stash
+//     for that k (shared memory); whenever a stash holds 32 particles the warp
+//     pushes them together, so short sub-cycles never diverge a warp and never
+//     leave the chip.  k >= kDeferMin: compacted into the queue of its k (one
+//     atomic per distinct k per warp) and deferred to the next launch.
+// Status byte inside a binned call: bits 0-2 = k_prev, bit 3 = step parity
+// (the stream of step j takes particles whose parity equals j & 1 and flips
+// it), bits 4-6 = deferred k (0 = none), bit 7 = lost.
 
-constexpr int kV = 4;                 // particles per lane in the bulk (128-bit loads)
-constexpr int kChunk = 32 * kV;       // particles per bulk work item
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kChunk = 256;          // particles per stream item (8 per lane)
+constexpr int kDeferMin = 3;         // smallest k that is deferred
+constexpr int kStashK = kDeferMin - 1;
+constexpr int kStashCap = 64;
 constexpr uint8_t kParity = 0x08;
 constexpr uint8_t kDeferMask = 0x70;
 
 __device__ __forceinline__ int deferred_k(uint8_t st) { return (st >> 4) & 7; }
 
-// Enqueue particle i into the queue of its k (1..7); warp-aggregated: one
-// atomic per distinct k in the warp.  All 32 lanes call this; key 0 = nothing.
+// Enqueue particle i into the queue of its k; warp-aggregated: one atomic per
+// distinct k in the warp.  All 32 lanes call this; key 0 = nothing.
 __device__ __forceinline__ void enqueue(const PushArgsMixed& a, int key, int32_t i) {
   const unsigned peers = __match_any_sync(0xffffffffu, key);
   const int lane = threadIdx.x & 31;
@@ -393,9 +473,50 @@ __device__ __forceinline__ void enqueue(const PushArgsMixed& a, int key, int32_t
   }
 }
 
-// Heavy item: finish the deferred previous step of particle i, then take its
-// criterion for the current step (push at once if k = 0, else defer again).
-// finalize: only finish the deferred step and write the public status.
+// A warp's stash of particles waiting for a short sub-cycle of one k.
+struct Stash {
+  int32_t idx[kStashCap];
+  int32_t cell[kStashCap];
+  float frac[kStashCap], ux[kStashCap], uy[kStashCap], uz[kStashCap];
+  uint8_t kp[kStashCap];
+};
+
+// Push the first `cnt` (<= 32) stashed particles, one per lane, with 4^k
+// sub-steps each; then move entries [cnt, n) to the front.  Warp-collective.
+template <int P>
+__device__ __forceinline__ void stash_drain(const PushArgsMixed& a, const StepFields<P>& F,
+                                            Stash& S, int k, int& n, int cnt,
+                                            unsigned long long* sh) {
+  const int lane = threadIdx.x & 31;
+  if (lane < cnt) {
+    MixedState s = {S.cell[lane], S.frac[lane], S.ux[lane], S.uy[lane], S.uz[lane]};
+    const int32_t i = S.idx[lane];
+    const bool ok = subcycle_f32<P>(F, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, a.field_time, a.mono,
+                                    k, S.kp[lane], 0.f, s);
+    normalize(s);
+    store_state(a, i, s);
+    a.status[i] = ok ? (uint8_t)(k | (a.parity_next ? kParity : 0)) : (uint8_t)(k | PIC_STATUS_LOST);
+    if (!ok) atomicAdd(&sh[11], 1ull);
+  }
+  __syncwarp();
+  const int rest = n - cnt;
+  if (lane < rest) {
+    const int q = cnt + lane;
+    S.idx[lane] = S.idx[q];
+    S.cell[lane] = S.cell[q];
+    S.frac[lane] = S.frac[q];
+    S.ux[lane] = S.ux[q];
+    S.uy[lane] = S.uy[q];
+    S.uz[lane] = S.uz[q];
+    S.kp[lane] = S.kp[q];
+  }
+  __syncwarp();
+  n = rest;
+}
+
+// Deferred item: finish the previous step of particle i, then take its
+// criterion for the current step (pushed at once if k < kDeferMin, else
+// deferred again).  finalize: only finish the deferred step (public status).
 template <int P>
 __device__ __forceinline__ void heavy_particle(const PushArgsMixed& a, const StepFields<P>& Fp,
                                                const StepFields<P>& Fc, const float* wcrit,
@@ -406,7 +527,8 @@ __device__ __forceinline__ void heavy_particle(const PushArgsMixed& a, const Ste
   const int k = deferred_k(st);
   const int k_prev = st & 7;
   MixedState s = load_state(a, i);
-  const bool ok = subcycle_f32<P>(Fp, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, a.field_time, k, k_prev, s);
+  const bool ok = subcycle_f32<P>(Fp, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, a.field_time, a.mono,
+                                  k, k_prev, 0.f, s);
   normalize(s);
   if (!ok) {
     store_state(a, i, s);
@@ -428,14 +550,16 @@ __device__ __forceinline__ void heavy_particle(const PushArgsMixed& a, const Ste
     return;
   }
   bool capped;
+  float b0;
   const int kn = criterion_f32<P>(Fc.B, wcrit, jb, wb, a.mask, s, a.qm_abs, a.dt, a.psi_max,
-                                  a.k_max, capped);
+                                  a.k_max, capped, b0);
   count_step(tc, sh, kn, capped);
-  if (kn == 0) {
-    const bool ok2 = subcycle_f32<P>(Fc, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, a.field_time, 0, k, s);
+  if (kn < kDeferMin) {
+    const bool ok2 = subcycle_f32<P>(Fc, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, a.field_time,
+                                     a.mono, kn, k, b0, s);
     normalize(s);
     store_state(a, i, s);
-    a.status[i] = ok2 ? (uint8_t)(a.parity_next ? kParity : 0) : (uint8_t)PIC_STATUS_LOST;
+    a.status[i] = ok2 ? (uint8_t)(kn | (a.parity_next ? kParity : 0)) : (uint8_t)(kn | PIC_STATUS_LOST);
     if (!ok2) atomicAdd(&sh[11], 1ull);
   } else {
     store_state(a, i, s);
@@ -444,11 +568,85 @@ __device__ __forceinline__ void heavy_particle(const PushArgsMixed& a, const Ste
   }
 }
 
+// Predicted item: particle i was binned before the launch as likely to
+// sub-cycle; take its exact criterion and all its sub-steps now.
 template <int P>
-__global__ void __launch_bounds__(256) push_mixed_binned_kernel(PushArgsMixed a) {
+__device__ __forceinline__ void predicted_particle(const PushArgsMixed& a, const StepFields<P>& Fc,
+                                                   const float* wcrit, int64_t i, ThreadCounters& tc,
+                                                   unsigned long long* sh) {
+  const uint8_t st = a.status[i];
+  const int k_prev = st & 7;
+  MixedState s = load_state(a, i);
+  int32_t je, jb;
+  float we, wb;
+  if (!tent_coords(s.cell, s.frac, Fc.lo, Fc.hi, je, we, jb, wb)) {
+    a.status[i] = (uint8_t)(k_prev | PIC_STATUS_LOST);
+    atomicAdd(&sh[11], 1ull);
+    return;
+  }
+  bool capped;
+  float b0;
+  const int k = criterion_f32<P>(Fc.B, wcrit, jb, wb, a.mask, s, a.qm_abs, a.dt, a.psi_max,
+                                 a.k_max, capped, b0);
+  count_step(tc, sh, k, capped);
+  const bool ok = subcycle_f32<P>(Fc, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, a.field_time, a.mono,
+                                  k, k_prev, b0, s);
+  normalize(s);
+  store_state(a, i, s);
+  a.status[i] = ok ? (uint8_t)(k | (a.parity_next ? kParity : 0)) : (uint8_t)(k | PIC_STATUS_LOST);
+  if (!ok) atomicAdd(&sh[11], 1ull);
+}
+
+// Before a predicted-schedule launch: particles the stream would take this
+// step and whose predicted k is > 0 go into the queue of that k, and their
+// parity bit is flipped so the stream leaves them to the predicted items.
+__global__ void bin_predicted_kernel(const uint8_t* pred, uint8_t* status, int64_t n,
+                                     int parity_cur, int32_t* pred_queue, int32_t* pred_count,
+                                     int64_t qcap) {
+  const uint8_t want = parity_cur ? kParity : 0;
+  const int64_t n_round = (n + 31) & ~(int64_t)31;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_round;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int key = 0;
+    if (i < n) {
+      const uint8_t st = status[i];
+      const int kp = pred[i];
+      if (!(st & PIC_STATUS_LOST) && !(st & kDeferMask) && ((st & kParity) == want) && kp > 0 &&
+          kp <= 7) {
+        status[i] = (uint8_t)(st ^ kParity);
+        key = kp;
+      }
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (key != 0 && lane == leader) base = atomicAdd(&pred_count[key], __popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (key != 0)
+      pred_queue[(int64_t)(key - 1) * qcap + base + __popc(peers & ((1u << lane) - 1u))] = (int32_t)i;
+  }
+}
+
+cudaError_t launch_bin_predicted(const uint8_t* pred, uint8_t* status, int64_t n, int parity_cur,
+                                 int32_t* pred_queue, int32_t* pred_count, int64_t qcap,
+                                 cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t want = (n + 255) / 256;
+  const int blocks = (int)(want < 152 * 8 ? want : 152 * 8);
+  bin_predicted_kernel<<<blocks, 256, 0, s>>>(pred, status, n, parity_cur, pred_queue, pred_count,
+                                              qcap);
+  return cudaGetLastError();
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads) push_binned_kernel(PushArgsMixed a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Stash* stashes = reinterpret_cast<Stash*>(smem);  // [kWarps][kStashK]
   __shared__ unsigned long long sh[12];
-  __shared__ int s_task[8];
-  __shared__ long long heavy_end[8];  // heavy items: ceil(count/32) per k, largest k first
+  __shared__ int s_task[kWarps];
+  __shared__ long long heavy_end[8];  // deferred items per k, largest k first (cumulative)
+  __shared__ long long pred_end[8];   // then predicted items
   if (threadIdx.x < 12) sh[threadIdx.x] = 0ull;
   if (threadIdx.x == 0) {
     long long acc = 0;
@@ -458,20 +656,34 @@ __global__ void __launch_bounds__(256) push_mixed_binned_kernel(PushArgsMixed a)
       acc += (c + 31) / 32;
       heavy_end[k] = acc;
     }
+    pred_end[0] = acc;
+    for (int k = 7; k >= 1; --k) {
+      const long long c = a.pred_count ? a.pred_count[k] : 0;
+      acc += (c + 31) / 32;
+      pred_end[k] = acc;
+    }
   }
   __syncthreads();
   constexpr int stride = 2 * (P + 1);
   const float* wcrit = a.wtab + a.crit_row * stride + (P + 1);
-  StepFields<P> Fc, Fp;
-  load_fields<P>(Fc, a.E, a.B, a.lo, a.hi);
+  const float* w0 = a.wtab + wrow(0, 1) * stride;  // theta = 1/2 weights of an m = 1 step
+  StepFields<P> F, Fp;
+  load_fields<P>(F, a.E, a.B, a.lo, a.hi);
   load_fields<P>(Fp, a.Ep, a.Bp, a.lo_p, a.hi_p);
   ThreadCounters tc;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-
+  Stash* my_stash = stashes + warp * kStashK;
+  int stash_n[kStashK];
+#pragma unroll
+  for (int q = 0; q < kStashK; ++q) stash_n[q] = 0;
+  const uint8_t want = a.parity_cur ? kParity : 0;
+  const uint8_t done = a.parity_next ? kParity : 0;
+  const float hx0 = __fmul_rn(a.dt, a.inv_dx);
   const int64_t n_heavy = heavy_end[1];
-  const int64_t n_bulk = a.finalize ? (a.n + kChunk - 1) / kChunk : (a.n + kChunk - 1) / kChunk;
-  const int64_t n_items = n_heavy + n_bulk;
+  const int64_t n_pred_end = pred_end[1];
+  const int64_t n_chunks = a.finalize ? 0 : (a.n + kChunk - 1) / kChunk;
+  const int64_t n_items = n_pred_end + n_chunks;
 
   for (;;) {
     if (lane == 0) s_task[warp] = atomicAdd(a.cursor, 1);
@@ -485,126 +697,129 @@ __global__ void __launch_bounds__(256) push_mixed_binned_kernel(PushArgsMixed a)
       const int64_t first = (k == 7 ? 0 : heavy_end[k + 1]);
       const int64_t e = (t - first) * 32 + lane;
       int key = 0;
+      int32_t i = 0;
       if (e < a.qcount_in[k]) {
-        const int32_t i = a.queue_in[(int64_t)(k - 1) * a.qcap + e];
-        heavy_particle<P>(a, Fp, Fc, wcrit, i, tc, sh, key);
-        enqueue(a, key, i);
-      } else {
-        enqueue(a, 0, 0);
+        i = a.queue_in[(int64_t)(k - 1) * a.qcap + e];
+        heavy_particle<P>(a, Fp, F, wcrit, i, tc, sh, key);
       }
+      enqueue(a, key, i);
       continue;
     }
-    // bulk item
-    const int64_t base = (t - n_heavy) * kChunk + (int64_t)lane * kV;
-    if (a.finalize) {
-      // return every byte to the public form (deferred ones are written by
-      // their heavy item)
-#pragma unroll
-      for (int v = 0; v < kV; ++v) {
-        const int64_t i = base + v;
-        if (i < a.n) {
-          const uint8_t st = a.status[i];
-          if ((st & kDeferMask) == 0) a.status[i] = (uint8_t)(st & (PIC_STATUS_LOST | 7));
-        }
-      }
+    if (t < n_pred_end) {
+      int k = 7;
+      while (k > 1 && t >= pred_end[k]) --k;
+      const int64_t first = (k == 7 ? n_heavy : pred_end[k + 1]);
+      const int64_t e = (t - first) * 32 + lane;
+      if (e < a.pred_count[k])
+        predicted_particle<P>(a, F, wcrit, a.pred_queue[(int64_t)(k - 1) * a.qcap + e], tc, sh);
       continue;
     }
-    const uint8_t want = a.parity_cur ? kParity : 0;
-    const bool full = base + kV <= a.n;
-    MixedState s[kV];
-    uint8_t st[kV];
-    if (full) {
-      const int4 c4 = *reinterpret_cast<const int4*>(a.cell + base);
-      const float4 f4 = *reinterpret_cast<const float4*>(a.frac + base);
-      const float4 x4 = *reinterpret_cast<const float4*>(a.px + base);
-      const float4 y4 = *reinterpret_cast<const float4*>(a.py + base);
-      const float4 z4 = *reinterpret_cast<const float4*>(a.pz + base);
-      const uint32_t s4 = *reinterpret_cast<const uint32_t*>(a.status + base);
-      s[0] = {c4.x, f4.x, x4.x, y4.x, z4.x};
-      s[1] = {c4.y, f4.y, x4.y, y4.y, z4.y};
-      s[2] = {c4.z, f4.z, x4.z, y4.z, z4.z};
-      s[3] = {c4.w, f4.w, x4.w, y4.w, z4.w};
-#pragma unroll
-      for (int v = 0; v < kV; ++v) st[v] = (uint8_t)(s4 >> (8 * v));
-    } else {
-#pragma unroll
-      for (int v = 0; v < kV; ++v) {
-        if (base + v < a.n) {
-          s[v] = load_state(a, base + v);
-          st[v] = a.status[base + v];
-        } else {
-          st[v] = PIC_STATUS_LOST;
-        }
-      }
+    // stream chunk
+    const int64_t c0 = (t - n_pred_end) * kChunk;
+    int64_t i = c0 + lane;
+    uint8_t st = PIC_STATUS_LOST;
+    MixedState s = {0, 0.5f, 0.f, 0.f, 0.f};
+    if (i < a.n) {
+      st = a.status[i];
+      s = load_state(a, i);
     }
-    bool owned_elsewhere = false;  // a lane particle belongs to the heavy items
-    bool touched[kV];
-#pragma unroll
-    for (int v = 0; v < kV; ++v) {
-      const bool valid = base + v < a.n;
-      const bool mine = valid && !(st[v] & PIC_STATUS_LOST) && !(st[v] & kDeferMask) &&
-                        ((st[v] & kParity) == want);
-      if (valid && !(st[v] & PIC_STATUS_LOST) && !mine) owned_elsewhere = true;
-      touched[v] = mine;
-      int key = 0;
+#pragma unroll 1
+    for (int r = 0; r < kChunk / 32; ++r, i += 32) {
+      const int64_t inext = i + 32;
+      uint8_t st_n = PIC_STATUS_LOST;
+      MixedState s_n = {0, 0.5f, 0.f, 0.f, 0.f};
+      if (r + 1 < kChunk / 32 && inext < a.n) {
+        st_n = a.status[inext];
+        s_n = load_state(a, inext);
+      }
+      const bool mine = i < a.n && !(st & PIC_STATUS_LOST) && !(st & kDeferMask) &&
+                        ((st & kParity) == want);
+      int key = 0, sk = 0;
       if (mine) {
         int32_t je, jb;
         float we, wb;
-        if (!tent_coords(s[v].cell, s[v].frac, Fc.lo, Fc.hi, je, we, jb, wb)) {
-          st[v] = (uint8_t)(st[v] | PIC_STATUS_LOST);
+        const bool inwin = tent_coords(s.cell, s.frac, F.lo, F.hi, je, we, jb, wb);
+        const float b0 = gather_f32<P>(F.B, wcrit, jb, wb, a.mask);
+        const float ey = gather_f32<P>(F.E, w0, je, we, a.mask);
+        if (!inwin) {
+          a.status[i] = (uint8_t)(st | PIC_STATUS_LOST);
           atomicAdd(&sh[11], 1ull);
         } else {
           bool capped;
-          const int k = criterion_f32<P>(Fc.B, wcrit, jb, wb, a.mask, s[v], a.qm_abs, a.dt,
-                                         a.psi_max, a.k_max, capped);
+          const int k = psi_to_k(b0, s, a.qm_abs, a.dt, a.psi_max, a.k_max, capped);
           count_step(tc, sh, k, capped);
-          const int k_prev = st[v] & 7;
+          const int k_prev = st & 7;
           if (k == 0) {
-            const bool ok = subcycle_f32<P>(Fc, a.wtab, a.mask, a.dt, a.inv_dx, a.qm,
-                                            a.field_time, 0, k_prev, s[v]);
-            normalize(s[v]);
-            st[v] = ok ? (uint8_t)(a.parity_next ? kParity : 0) : (uint8_t)PIC_STATUS_LOST;
-            if (!ok) atomicAdd(&sh[11], 1ull);
+            const float h_old = ldexpf(a.dt, -2 * k_prev);
+            const float hp = __fmul_rn(0.5f, __fadd_rn(h_old, a.dt));
+            boris_f32(ey, b0, hp, hx0, a.qm, s);
+            normalize(s);
+            store_state(a, i, s);
+            a.status[i] = done;
+          } else if (k < kDeferMin) {
+            sk = k;
           } else {
-            st[v] = (uint8_t)(k_prev | (k << 4));
+            a.status[i] = (uint8_t)(k_prev | (k << 4));
             key = k;
           }
         }
       }
-      enqueue(a, key, (int32_t)(base + v));
-    }
-    if (full && !owned_elsewhere) {
-      *reinterpret_cast<int4*>(a.cell + base) = make_int4(s[0].cell, s[1].cell, s[2].cell, s[3].cell);
-      *reinterpret_cast<float4*>(a.frac + base) = make_float4(s[0].frac, s[1].frac, s[2].frac, s[3].frac);
-      *reinterpret_cast<float4*>(a.px + base) = make_float4(s[0].ux, s[1].ux, s[2].ux, s[3].ux);
-      *reinterpret_cast<float4*>(a.py + base) = make_float4(s[0].uy, s[1].uy, s[2].uy, s[3].uy);
-      *reinterpret_cast<float4*>(a.pz + base) = make_float4(s[0].uz, s[1].uz, s[2].uz, s[3].uz);
-      *reinterpret_cast<uint32_t*>(a.status + base) =
-          (uint32_t)st[0] | ((uint32_t)st[1] << 8) | ((uint32_t)st[2] << 16) | ((uint32_t)st[3] << 24);
-    } else {
+      enqueue(a, key, (int32_t)i);
+      // park k = 1, 2 in the warp's stashes; push a stash when it holds 32
 #pragma unroll
-      for (int v = 0; v < kV; ++v) {
-        if (touched[v]) {
-          store_state(a, base + v, s[v]);
-          a.status[base + v] = st[v];
+      for (int q = 0; q < kStashK; ++q) {
+        const unsigned m = __ballot_sync(0xffffffffu, sk == q + 1);
+        if (m == 0u) continue;
+        Stash& S = my_stash[q];
+        if (sk == q + 1) {
+          const int pos = stash_n[q] + __popc(m & ((1u << lane) - 1u));
+          S.idx[pos] = (int32_t)i;
+          S.cell[pos] = s.cell;
+          S.frac[pos] = s.frac;
+          S.ux[pos] = s.ux;
+          S.uy[pos] = s.uy;
+          S.uz[pos] = s.uz;
+          S.kp[pos] = (uint8_t)(st & 7);
         }
+        stash_n[q] += __popc(m);
+        __syncwarp();
+        if (stash_n[q] >= 32) stash_drain<P>(a, F, S, q + 1, stash_n[q], 32, sh);
       }
+      st = st_n;
+      s = s_n;
     }
   }
+  // push what is left in the stashes
+#pragma unroll
+  for (int q = 0; q < kStashK; ++q)
+    if (stash_n[q] > 0) stash_drain<P>(a, F, my_stash[q], q + 1, stash_n[q], stash_n[q], sh);
   flush_counters(tc, sh, a.stats);
 
   // the last block to finish resets the cursor and the consumed queue counts
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    const unsigned done = atomicAdd(a.blocks_done, 1u);
-    if (done == gridDim.x - 1) {
+    const unsigned fin = atomicAdd(a.blocks_done, 1u);
+    if (fin == gridDim.x - 1) {
       __threadfence();
       *a.cursor = 0;
       *a.blocks_done = 0;
       for (int k = 0; k < 8; ++k) a.qcount_in[k] = 0;
+      if (a.pred_count)
+        for (int k = 0; k < 8; ++k) a.pred_count[k] = 0;
       __threadfence();
     }
+  }
+}
+
+// After the closing launch of a call: every status byte back to the public
+// form (k | lost).  Deferred particles were written by that launch.
+__global__ void reset_status_kernel(uint8_t* status, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint8_t st = status[i];
+    const uint8_t pub = (uint8_t)(st & (PIC_STATUS_LOST | 7));
+    if (pub != st) status[i] = pub;
   }
 }
 
@@ -662,41 +877,71 @@ cudaError_t launch_features_mixed(const PushArgsMixed& a, int order, float* phi,
 // ---------------------------------------------------------------- launch
 
 template <int P>
-static cudaError_t launch_p(const PushArgsMixed& a, int schedule, int sm_count, cudaStream_t s) {
+static cudaError_t launch_p(const PushArgsMixed& a, int schedule, int sm_count, cudaStream_t s,
+                            int* launches) {
   const int sms = sm_count > 0 ? sm_count : 152;
-  if (schedule == PIC_SCHED_BINNED) {
-    static int occ = 0;
-    if (occ == 0) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, push_mixed_binned_kernel<P>, 256, 0);
-      if (occ < 1) occ = 1;
-    }
-    const int64_t items = (a.n + kChunk - 1) / kChunk;
-    int64_t blocks = (int64_t)sms * occ;
-    const int64_t need = (items + 7) / 8 + 1;
-    if (blocks > need) blocks = need;
-    push_mixed_binned_kernel<P><<<(int)blocks, 256, 0, s>>>(a);
-  } else {
+  if (schedule == PIC_SCHED_PLAIN) {
     const int64_t want = (a.n + 255) / 256;
     const int64_t cap = (int64_t)sms * 8;
     push_mixed_plain_kernel<P><<<(int)(want < cap ? want : cap), 256, 0, s>>>(a);
+    if (launches) ++*launches;
   }
+  return cudaGetLastError();
+}
+
+constexpr size_t kStashBytes = sizeof(Stash) * kWarps * kStashK;
+
+template <int P>
+static cudaError_t launch_binned_p(const PushArgsMixed& a, int sm_count, cudaStream_t main,
+                                   int* launches) {
+  const int sms = sm_count > 0 ? sm_count : 152;
+  static int occ = 0;
+  if (occ == 0) {
+    cudaError_t e = cudaFuncSetAttribute(push_binned_kernel<P>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStashBytes);
+    if (e != cudaSuccess) return e;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, push_binned_kernel<P>, kThreads, kStashBytes);
+    if (occ < 1) occ = 1;
+  }
+  int64_t blocks = (int64_t)sms * occ;
+  const int64_t items = (a.n + kChunk - 1) / kChunk;
+  if (!a.finalize && blocks > (items + kWarps - 1) / kWarps + sms) blocks = (items + kWarps - 1) / kWarps + sms;
+  push_binned_kernel<P><<<(int)blocks, kThreads, kStashBytes, main>>>(a);
+  int n = 1;
+  if (a.finalize) {
+    const int64_t want = (a.n + 255) / 256;
+    reset_status_kernel<<<(int)(want < sms * 8 ? want : sms * 8), 256, 0, main>>>(a.status, a.n);
+    ++n;
+  }
+  if (launches) *launches += n;
   return cudaGetLastError();
 }
 
 cudaError_t launch_push_mixed(const PushArgsMixed& a, int order, int schedule, int sm_count,
                               cudaStream_t s, int* launches) {
   if (a.n <= 0) return cudaSuccess;
-  cudaError_t e;
+  if (schedule != PIC_SCHED_PLAIN) return launch_binned_step(a, order, sm_count, s, launches);
   switch (order) {
-    case 1: e = launch_p<1>(a, schedule, sm_count, s); break;
-    case 2: e = launch_p<2>(a, schedule, sm_count, s); break;
-    case 3: e = launch_p<3>(a, schedule, sm_count, s); break;
-    case 4: e = launch_p<4>(a, schedule, sm_count, s); break;
-    case 5: e = launch_p<5>(a, schedule, sm_count, s); break;
+    case 1: return launch_p<1>(a, schedule, sm_count, s, launches);
+    case 2: return launch_p<2>(a, schedule, sm_count, s, launches);
+    case 3: return launch_p<3>(a, schedule, sm_count, s, launches);
+    case 4: return launch_p<4>(a, schedule, sm_count, s, launches);
+    case 5: return launch_p<5>(a, schedule, sm_count, s, launches);
     default: return cudaErrorInvalidValue;
   }
-  if (launches) ++*launches;
-  return e;
+}
+
+cudaError_t launch_binned_step(const PushArgsMixed& a, int order, int sm_count, cudaStream_t main,
+                               int* launches) {
+  if (a.n <= 0) return cudaSuccess;
+  switch (order) {
+    case 1: return launch_binned_p<1>(a, sm_count, main, launches);
+    case 2: return launch_binned_p<2>(a, sm_count, main, launches);
+    case 3: return launch_binned_p<3>(a, sm_count, main, launches);
+    case 4: return launch_binned_p<4>(a, sm_count, main, launches);
+    case 5: return launch_binned_p<5>(a, sm_count, main, launches);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace pic

@@ -30,7 +30,7 @@ struct NoAllocScratch {
   double wtab64[kRows * kMaxStride];
   float wtab32[kRows * kMaxStride];
   int32_t queue[2 * 7 * kNoAllocMaxParticles];
-  int32_t qcount[64];  // [0,16): per-k counts of both queue sets; 16: cursor; 17: blocks done
+  int32_t qcount[64];  // [0,16): per-k counts of both queue sets; 16: cursor; 18: blocks done
   DevStats stats;
 };
 
@@ -153,12 +153,13 @@ extern "C" int pic_push_mixed_noalloc(const pic_params* prm, int64_t n_particles
   base.inv_dx = (float)(1.0 / prm->dx);
   base.k_max = prm->k_max;
   base.field_time = prm->field_time;
+  lagrange_monomials(p, base.mono);
   base.wtab = S->wtab32;
   base.crit_row = wrows_total(prm->k_max) - 1;
   base.stats = &S->stats;
   base.qcap = kNoAllocMaxParticles;
   base.cursor = (int*)(S->qcount + 16);
-  base.blocks_done = (unsigned*)(S->qcount + 17);
+  base.blocks_done = (unsigned*)(S->qcount + 18);
   const int64_t qsz = 7 * kNoAllocMaxParticles;
 
   if (n_particles > 0) {

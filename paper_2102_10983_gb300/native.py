@@ -18,7 +18,7 @@ from . import build as _build
 PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA, PIC_ERANGE, PIC_EKMAX, PIC_ETIMEOUT = range(7)
 PIC_HOST, PIC_DEVICE = 0, 1
 PIC_FP64, PIC_MIXED = 0, 1
-PIC_SCHED_PLAIN, PIC_SCHED_BINNED = 0, 1
+PIC_SCHED_PLAIN, PIC_SCHED_BINNED, PIC_SCHED_PREDICTED = 0, 1, 2
 PIC_STATUS_LOST = 0x80
 
 ERR_NAMES = {0: "PIC_OK", 1: "PIC_EINVAL", 2: "PIC_ENOMEM", 3: "PIC_ECUDA", 4: "PIC_ERANGE",
@@ -60,6 +60,7 @@ SIGNATURES = {
     "pic_launch_count": (ctypes.c_int64, [_VP]),
     "pic_last_error": (ctypes.c_char_p, [_VP]),
     "pic_features": (ctypes.c_int, [_VP, _I64, _VP]),
+    "pic_attach_predictor": (ctypes.c_int, [_VP, _VP, _I32]),
     "pic_mlp_param_count": (ctypes.c_int, []),
     "pic_mlp_create": (ctypes.c_int, [ctypes.c_uint64, _VP, ctypes.POINTER(_VP)]),
     "pic_mlp_destroy": (ctypes.c_int, [_VP]),
@@ -200,6 +201,10 @@ class Integrator:
         st = PicStepStats()
         _check(lib().pic_stats_read(self.ctx, ctypes.byref(st), 1 if reset else 0), self.ctx)
         return st
+
+    def attach_predictor(self, predictor: "Predictor", every: int = 1):
+        _check(lib().pic_attach_predictor(self.ctx, predictor.h, int(every)), self.ctx)
+        self._predictor = predictor
 
     def timing(self, on: bool = True):
         _check(lib().pic_timing_enable(self.ctx, 1 if on else 0), self.ctx)

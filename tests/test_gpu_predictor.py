@@ -123,7 +123,9 @@ def test_features_kernel_matches_definition():
 
     want = omlp.features(gather(E, wE, s_), gather(B, wB, s_ - 0.5), px, py, pz)
     got = phi.cpu().numpy().astype(np.float64)
-    np.testing.assert_allclose(got, want, rtol=2e-5, atol=2e-4)
+    alive = (st & native.PIC_STATUS_LOST) == 0
+    assert alive.mean() > 0.9
+    np.testing.assert_allclose(got[alive], want[alive], rtol=2e-5, atol=2e-4)
 
 
 def test_training_on_logged_pairs_learns_the_next_k():

@@ -64,3 +64,32 @@ def test_binned_bitwise_other_orders_and_window_exit(order):
         np.testing.assert_array_equal(u, v)
     assert sa.out_of_window == sb.out_of_window
     assert list(sa.k_hist) == list(sb.k_hist)
+
+
+def _run_pred(wl, n_steps, call_lens, predictor, every, order=3):
+    integ = native.Integrator(wl.dt, wl.dx, wl.psi_max, order=order, precision=native.PIC_MIXED,
+                              schedule=native.PIC_SCHED_PREDICTED, capacity=wl.n_particles,
+                              window=wl.window, ring_levels=order + 2 + max(call_lens))
+    integ.attach_predictor(predictor, every)
+    ini = wl.particles()
+    integ.pic_particles_write(ini.x, ini.px, ini.py, ini.pz)
+    st = H.run_gpu_calls(integ, wl, order, 0, n_steps, call_lens)
+    out = integ.read_numpy()
+    integ.close()
+    return out, st
+
+
+@pytest.mark.parametrize("every", [1, 5])
+def test_predicted_bitwise_equals_plain_even_with_an_untrained_network(every):
+    """The network only orders the work: with random weights it mispredicts
+    most sub-cycling electrons, and the results are still the plain bits."""
+    wl = _wl(5000)
+    net = native.Predictor(seed=123)
+    a, sa = _run(wl, native.PIC_SCHED_PLAIN, 1200, [7, 64, 3])
+    b, sb = _run_pred(wl, 1200, [7, 64, 3], net, every)
+    assert sa.k_hist[5] > 0
+    for u, v in zip(a, b):
+        np.testing.assert_array_equal(u, v)
+    assert list(sa.k_hist) == list(sb.k_hist)
+    assert (sa.substeps, sa.n_star, sa.out_of_window) == (sb.substeps, sb.n_star, sb.out_of_window)
+    net.close()
