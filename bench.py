@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--acc-particles", type=int, default=524288)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-steps", type=int, default=200)
+    ap.add_argument("--batched-ensembles", type=int, default=512)
     ap.add_argument("--cpu-sample", type=int, default=16384)
     return ap.parse_args()
 
@@ -80,6 +83,17 @@ def barrier(ws):
     if ws > 1:
         import torch.distributed as dist
         dist.barrier()
+
+
+def aggregate_value(units_per_rank: int, steps: int, ws: int, ms_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * steps * ws / (ms_max / 1e3)
+
+
+def rank_workload(rank: int, n_particles: int, order: int) -> W.Workload:
+    """Weak scaling: every rank pushes its own electrons (its own seed), same shape."""
+    return W.Workload(**{**W.C2.__dict__, "n_particles": n_particles, "seed": W.C2.seed + rank,
+                         "order": order})
 
 
 def max_over_ranks(ws, v):
@@ -240,6 +254,84 @@ def accuracy_run(wl, ini, n_acc, steps, E, B, i0, ring, stream, dev, sched, sens
     return res
 
 
+def batched_workload(n_ens: int, seed: int = 3):
+    """512 independent ensembles cycling a0 x resolution x Psi_max over
+    {10, 30, 100, 300} x {25, 50, 75, 150} x {0.003, 0.01, 0.03}; sizes
+    log-uniform in [1e3, 1e6] from the seed; electrons at rest, x0 in [0, lambda);
+    c dt/dx = 0.99; third order."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sizes = np.round(np.exp(rng.uniform(np.log(1e3), np.log(1e6), n_ens))).astype(np.int64)
+    a0s, ress, psis = (10.0, 30.0, 100.0, 300.0), (25, 50, 75, 150), (0.003, 0.01, 0.03)
+    ens = []
+    for q in range(n_ens):
+        a0 = a0s[q % 4]
+        res = ress[(q // 4) % 4]
+        psi = psis[(q // 16) % 3]
+        dt = 2 * math.pi / res
+        dx = dt / 0.99
+        wl = W.Workload(name=f"ens{q}", n_particles=int(sizes[q]), a0=a0, dt=dt, dx=dx,
+                        psi_max=psi, order=3, n_steps=5000, x_lo=0.0, x_hi=2 * math.pi,
+                        seed=1000 + q, window=512, lead=int(math.ceil(2 * math.pi / dx)) + 16,
+                        sort_x=True)
+        ens.append(wl)
+    return ens
+
+
+def run_batched(args, dev, stream):
+    """The batched ensembles: autotuned, graph-captured multi-step launch."""
+    import torch
+    from paper_2102_10983_gb300 import native
+    ens = batched_workload(args.batched_ensembles)
+    p, K, Wn = 3, args.batched_steps, 512
+    b = native.Batch([dict(dt=wl.dt, dx=wl.dx, psi_max=wl.psi_max, n_particles=wl.n_particles)
+                      for wl in ens], order=p, window=Wn, ring_levels=K + p + 8, stream=stream)
+    inis = [wl.particles() for wl in ens]
+    b.particles_write(*[np.concatenate([getattr(i, f) for i in inis]) for f in ("x", "px", "py", "pz")])
+    del inis
+    n_total = b.n_total
+    # levels -p .. K+3 of every ensemble, generated on the device
+    dts = torch.tensor([wl.dt for wl in ens], dtype=torch.float64, device=dev)[:, None]
+    dxs = torch.tensor([wl.dx for wl in ens], dtype=torch.float64, device=dev)[:, None]
+    a0s = torch.tensor([wl.a0 for wl in ens], dtype=torch.float64, device=dev)[:, None]
+    c = torch.arange(Wn, dtype=torch.float64, device=dev)[None, :]
+    origins = np.stack([wl.origins(-p, K + p + 4) for wl in ens])  # (n_ens, levels)
+
+    def level(r):
+        n = float(r - p)
+        i0 = torch.as_tensor(origins[:, r], dtype=torch.float64, device=dev)[:, None]
+        xiE = n * dts - (i0 + c) * dxs
+        xiB = (n + 0.5) * dts - (i0 + c + 0.5) * dxs
+        E = torch.where(xiE > 0, -a0s * torch.cos(xiE), torch.zeros_like(xiE)).contiguous()
+        B = torch.where(xiB > 0, -a0s * torch.cos(xiB), torch.zeros_like(xiB)).contiguous()
+        return origins[:, r], E, B
+
+    for r in range(K + p + 4):
+        i0, E, B = level(r)
+        b.fields_upload(r - p, i0, E, B)
+    chunk, blocks, tune_ms = b.autotune(0, 4)
+    b.config(chunk=chunk, blocks_per_sm=blocks, use_graph=True)
+    torch.cuda.synchronize()
+    launches0 = b.launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st = b.push_step(0, K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    out = {"workload": f"{len(ens)} ensembles, a0 x lambda/(c dt) x Psi_max cycled over "
+                       "{10,30,100,300} x {25,50,75,150} x {0.003,0.01,0.03}, sizes log-uniform "
+                       "[1e3, 1e6], electrons at rest, steps 0..%d" % (K - 1),
+           "electrons": int(n_total), "steps": K,
+           "value": n_total * K / (ms / 1e3), "unit": UNIT,
+           "substeps_per_s": st.substeps / (ms / 1e3),
+           "ms_per_step": ms / K, "autotuned": {"chunk": chunk, "blocks_per_sm": blocks,
+                                                 "trial_ms_per_step": tune_ms},
+           "graph_captured": True, "gpu_launches": b.launches() - launches0,
+           "k_hist": list(st.k_hist), "out_of_window": st.out_of_window}
+    b.close()
+    return out
+
+
 # ---------------------------------------------------------------- our arm
 
 def run_ours(args, ws, rank, local):
@@ -249,8 +341,7 @@ def run_ours(args, ws, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    wl = W.Workload(**{**W.C2.__dict__, "n_particles": args.particles, "seed": W.C2.seed + rank,
-                       "order": args.order})
+    wl = rank_workload(rank, args.particles, args.order)
     p = wl.order
     start, Wu, K = args.start_step, args.warmup, args.steps
     last = start + Wu + K
@@ -299,7 +390,7 @@ def run_ours(args, ws, rank, local):
     st = integ.pic_stats_read(reset=True)
     integ.close()
     total_ms = max_over_ranks(ws, total_ms)
-    ps = n_e * K * ws / (total_ms / 1e3)
+    ps = aggregate_value(n_e, K, ws, total_ms)
     substeps = max(st.substeps, 1)
     out.update(value=ps, ms_per_step=total_ms / K, launches=launches, clocks=clk,
                kern_ms=kern_ms / max(kern_steps, 1), stats=st.as_dict(),
@@ -373,6 +464,8 @@ def run_ours(args, ws, rank, local):
         out["e2e"] = {"value": n_e * Ke * ws / e2e_s, "unit": UNIT, "steps": Ke,
                       "h2d_bytes_per_step": 2 * wl.window * 8,
                       "d2h_bytes_per_step": int(native.ctypes.sizeof(native.PicStepStats))}
+    if not args.no_batched:
+        out["batched"] = run_batched(args, dev, stream)
     return wl, out
 
 
@@ -411,16 +504,20 @@ def run_reference(args, ws, rank):
     parts = oracle.Particles(ini.x, ini.px, ini.py, ini.pz)
     oracle.lib()
     start, Wu, K = args.start_step, args.warmup, args.steps
-    # the sample walks from step 0; only steps start+Wu .. start+Wu+K are timed
-    E, B, i0 = wl.levels(-p, start + Wu + K + p)
-    if start + Wu > 0:
-        oracle.run(prm, parts, E[: start + Wu + p], i0[: start + Wu + p],
-                   B[: start + Wu + p], i0[: start + Wu + p])
-    t0 = time.perf_counter()
-    for s in range(start + Wu, start + Wu + K):
-        r = s  # row of level s - p
-        oracle.run(prm, parts, E[r: r + p + 1], i0[r: r + p + 1], B[r: r + p + 1], i0[r: r + p + 1])
-    el = time.perf_counter() - t0
+    # the sample walks from step 0; only steps start+Wu .. start+Wu+K-1 are timed
+    # (levels are generated in chunks, outside the timed calls)
+    el = 0.0
+    s, end = 0, start + Wu + K
+    while s < end:
+        c = min(500, end - s)
+        if s < start + Wu:
+            c = min(c, start + Wu - s)
+        E, B, i0 = wl.levels(s - p, c + p)
+        t0 = time.perf_counter()
+        oracle.run(prm, parts, E, i0, B, i0)
+        if s >= start + Wu:
+            el += time.perf_counter() - t0
+        s += c
     v = n_s * K / el
     return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": K,
             "warmup": Wu, "ms_per_step": el * 1e3 / K, "higher_is_better": True,
@@ -460,6 +557,7 @@ def main():
                    "order": wl.order, "form": "mixed", "schedule": args.schedule,
                    "start_step": args.start_step,
                    "l2": "inputs larger than L2 (352 MB particle state per GPU)",
+                   "layout": "electrons stored in order of initial position, never re-sorted",
                    "parallelism": f"replicas x{ws}"},
         "substeps_per_s": out["substeps_per_s"],
         "fp64_value": out.get("fp64_value"), "fp64_steps": out.get("fp64_steps"),
@@ -475,6 +573,8 @@ def main():
     }
     if "e2e" in out:
         line["e2e"] = out["e2e"]
+    if "batched" in out:
+        line["batched"] = out["batched"]
     if not args.no_cpu_baseline:
         v, _ = cpu_baseline(wl, args.cpu_sample, 1000)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",

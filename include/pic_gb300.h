@@ -219,6 +219,67 @@ int pic_mlp_train_step(pic_mlp* mlp, const float* phi, const uint8_t* label, int
  * samples: pred is device n uint8.  Asynchronous. */
 int pic_mlp_infer(pic_mlp* mlp, const float* phi, int64_t n, uint8_t* pred);
 
+/* ---- batched ensembles (not in the paper) -----------------------------------
+ * Many independent problems (each its own dt, dx, Psi_max, q/m, k cap, field-
+ * time reading, particle count and field window) advanced together: one store,
+ * one persistent launch per macro step (mixed form, binned schedule); all share
+ * the Lagrange order p and the window size W.  Particles of ensemble e occupy
+ * positions [first_e, first_e + n_e) of the concatenated arrays, in ensemble
+ * order. */
+typedef struct {
+  double dt, dx, psi_max, qm;
+  int32_t k_max, field_time;
+  int64_t n_particles;
+} pic_ensemble;
+
+typedef struct pic_batch pic_batch;
+
+/* Create a batch of n_ens (1..65535) ensembles; window_cells a power of two in
+ * [16, 2^28]; ring_levels >= order + 2.  Errors: PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA. */
+int pic_batch_create(const pic_ensemble* ens, int32_t n_ens, int32_t order,
+                     int64_t window_cells, int32_t ring_levels, void* stream, pic_batch** out);
+int pic_batch_destroy(pic_batch* b);
+
+/* Stream chunk length (a multiple of 32 in [32, 8192]), resident blocks per SM
+ * (1 .. the kernel's occupancy) and whether multi-step pic_batch_push_step
+ * calls are captured into one CUDA graph and launched as such (needs a
+ * non-NULL stream). */
+int pic_batch_config(pic_batch* b, int32_t chunk, int32_t blocks_per_sm, int32_t use_graph);
+
+/* Load / read all particles, concatenated in ensemble order (FP64 in and out,
+ * mixed layout inside; status as for pic_particles_write). */
+int pic_batch_particles_write(pic_batch* b, const double* x, const double* px, const double* py,
+                              const double* pz, const uint8_t* status, int32_t where);
+int pic_batch_particles_read(pic_batch* b, double* x, double* px, double* py, double* pz,
+                             uint8_t* status, int32_t where);
+
+/* Level `level` of every ensemble: i0 (host, n_ens) the window origins; Ey and
+ * Bz n_ens x W FP64 in `where` memory (ensemble-major).  Same grid convention
+ * as pic_fields_upload. */
+int pic_batch_fields_upload(pic_batch* b, int64_t level, const int64_t* i0, const double* Ey,
+                            const double* Bz, int32_t where);
+
+/* Macro steps n .. n+n_steps-1 of every ensemble (stats: totals over the
+ * batch; as for pic_push_step). */
+int pic_batch_push_step(pic_batch* b, int64_t n, int64_t n_steps, pic_step_stats* stats);
+
+/* Event timing of each pushed step: on/off; with non-NULL outputs, also return
+ * (and reset) the summed milliseconds and the number of timed steps. */
+int pic_batch_timing(pic_batch* b, int32_t on, double* total_ms, int64_t* steps);
+
+/* Kernel launches queued so far. */
+int64_t pic_batch_launch_count(const pic_batch* b);
+
+/* Pick the stream chunk length and blocks per SM: every candidate runs `steps`
+ * macro steps from step n, each from the same saved particle state (restored
+ * afterwards); the fastest is kept and returned (ms per step in ms_out).  The
+ * levels of steps n .. n+steps-1 must be in the ring.  Allocates a temporary
+ * copy of the particle state. */
+int pic_batch_autotune(pic_batch* b, int64_t n, int32_t steps, int32_t* chunk_out,
+                       int32_t* blocks_out, double* ms_out);
+
+const char* pic_batch_last_error(const pic_batch* b);
+
 /* Allocation-free variant of the binned mixed-precision push (no counterpart
  * in the paper: it exists for host programs that may not call cudaMalloc at
  * push time, e.g. because another framework owns and carves up all device

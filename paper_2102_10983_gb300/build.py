@@ -25,6 +25,8 @@ SOURCES = {
     "push_f64.cu": ["-fmad=false"],
     "push_mixed.cu": [],
     "push_noalloc.cu": [],
+    "push_batch.cu": [],
+    "batch_api.cu": [],
     "mlp_bf16.cu": [],
     "mlp_api.cu": [],
 }
@@ -38,7 +40,7 @@ def _nvcc() -> str:
 
 
 def _deps():
-    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
+    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]  # .cu, .cuh, .h
     files += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
     files.append(os.path.abspath(__file__))
     return files

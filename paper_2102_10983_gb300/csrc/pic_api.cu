@@ -41,6 +41,7 @@ struct pic_ctx {
   // predicted schedule
   uint8_t* pred = nullptr;
   float* phi = nullptr;
+  float* half = nullptr;  // mixed form: E_y, B_z of every window node at the step's t_n
   int32_t* pred_queue = nullptr;
   const pic_mlp* mlp = nullptr;
   int32_t predict_every = 1;
@@ -85,7 +86,7 @@ static void free_all(pic_ctx* c) {
 
   void* ptrs[] = {c->x, c->px, c->py, c->pz, c->cell, c->frac, c->fpx, c->fpy, c->fpz,
                   c->status, c->ringE, c->ringB, c->staging, c->wtab64, c->wtab32,
-                  c->dstats, c->queue, c->qcount, c->pred, c->phi, c->pred_queue};
+                  c->dstats, c->queue, c->qcount, c->pred, c->phi, c->pred_queue, c->half};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -136,6 +137,24 @@ __global__ void from_mixed_kernel(const int32_t* cell, const float* frac, const 
   }
 }
 
+cudaError_t pic::launch_to_mixed(const double* x, const double* px, const double* py,
+                                 const double* pz, int32_t* cell, float* frac, float* fpx,
+                                 float* fpy, float* fpz, double inv_dx, int64_t n, cudaStream_t s) {
+  const int64_t want = (n + 255) / 256;
+  to_mixed_kernel<<<(int)(want < 152 * 16 ? (want > 0 ? want : 1) : 152 * 16), 256, 0, s>>>(
+      x, px, py, pz, cell, frac, fpx, fpy, fpz, inv_dx, n);
+  return cudaGetLastError();
+}
+
+cudaError_t pic::launch_from_mixed(const int32_t* cell, const float* frac, const float* fpx,
+                                   const float* fpy, const float* fpz, double* x, double* px,
+                                   double* py, double* pz, double dx, int64_t n, cudaStream_t s) {
+  const int64_t want = (n + 255) / 256;
+  from_mixed_kernel<<<(int)(want < 152 * 16 ? (want > 0 ? want : 1) : 152 * 16), 256, 0, s>>>(
+      cell, frac, fpx, fpy, fpz, x, px, py, pz, dx, n);
+  return cudaGetLastError();
+}
+
 static int grid_for(const pic_ctx* c, int64_t n) {
   int64_t b = (n + 255) / 256;
   int64_t cap = (int64_t)(c->sm_count > 0 ? c->sm_count : 152) * 16;
@@ -169,6 +188,8 @@ extern "C" int pic_create(const pic_params* prm, int64_t capacity, int64_t windo
     return fail(nullptr, PIC_EINVAL, "pic_create: capacity must be 0..2^31-1%s");
   if (!is_pow2(window_cells) || window_cells < 16 || window_cells > ((int64_t)1 << 30))
     return fail(nullptr, PIC_EINVAL, "pic_create: window_cells must be a power of two >= 16%s");
+  if (prm->precision == PIC_MIXED && window_cells > ((int64_t)1 << 28))
+    return fail(nullptr, PIC_EINVAL, "pic_create: the mixed form takes window_cells <= 2^28%s");
   if (ring_levels < prm->order + 1 || ring_levels > (1 << 20))
     return fail(nullptr, PIC_EINVAL, "pic_create: ring_levels must be >= order + 1%s");
   if (prm->schedule != PIC_SCHED_PLAIN && ring_levels < prm->order + 2)
@@ -195,6 +216,7 @@ extern "C" int pic_create(const pic_params* prm, int64_t capacity, int64_t windo
     if (e == cudaSuccess) e = cudaMalloc(p, bytes);
   };
   if (mixed) {
+    A((void**)&c->half, 2 * (size_t)window_cells * 4);
     A((void**)&c->cell, cap * 4);
     A((void**)&c->frac, cap * 4);
     A((void**)&c->fpx, cap * 4);
@@ -216,8 +238,10 @@ extern "C" int pic_create(const pic_params* prm, int64_t capacity, int64_t windo
     A((void**)&c->pz, cap * 8);
   }
   A((void**)&c->status, cap);
-  A(&c->ringE, (size_t)ring_levels * window_cells * fsz);
-  A(&c->ringB, (size_t)ring_levels * window_cells * fsz);
+  // the mixed form's ring is mirrored (2R slots, see PushArgsMixed)
+  const size_t ring_slots = (size_t)ring_levels * (mixed ? 2 : 1);
+  A(&c->ringE, ring_slots * window_cells * fsz);
+  A(&c->ringB, ring_slots * window_cells * fsz);
   c->staging_len = 2 * window_cells;
   if (c->staging_len < ((int64_t)1 << 22)) c->staging_len = (int64_t)1 << 22;
   A((void**)&c->staging, (size_t)c->staging_len * 8);
@@ -424,9 +448,16 @@ extern "C" int pic_fields_upload(pic_ctx* c, int64_t level, int64_t i0, const do
     double* sB = (double*)c->ringB + (int64_t)slot * W;
     scatter_level_kernel<double><<<blocks, 256, 0, c->stream>>>(sE, sB, e, b, i0, W);
   } else {
-    float* sE = (float*)c->ringE + (int64_t)slot * W;
-    float* sB = (float*)c->ringB + (int64_t)slot * W;
-    scatter_level_kernel<float><<<blocks, 256, 0, c->stream>>>(sE, sB, e, b, i0, W);
+    for (int copy = 0; copy < 2; ++copy) {
+      float* sE = (float*)c->ringE + ((int64_t)slot + (int64_t)copy * c->R) * W;
+      float* sB = (float*)c->ringB + ((int64_t)slot + (int64_t)copy * c->R) * W;
+      scatter_level_kernel<float><<<blocks, 256, 0, c->stream>>>(sE, sB, e, b, i0, W);
+      ++c->launches;
+    }
+    CUDA_TRY(c, cudaGetLastError());
+    c->slot_level[slot] = level;
+    c->slot_i0[slot] = i0;
+    return PIC_OK;
   }
   ++c->launches;
   CUDA_TRY(c, cudaGetLastError());
@@ -478,12 +509,17 @@ static int step_slots(pic_ctx* c, int64_t s, int* slots, int64_t* lo, int64_t* h
   return PIC_OK;
 }
 
-static void fill_mixed(pic_ctx* c, PushArgsMixed& a, const int* slots, int64_t lo, int64_t hi,
-                       bool prev) {
+// Field arguments of step s (prev: as the previous step's fields) for the mixed
+// form: the start slot of its p+1 consecutive levels in the mirrored ring.
+static void fill_mixed(pic_ctx* c, PushArgsMixed& a, int64_t s, int64_t lo, int64_t hi, bool prev) {
   const int p = c->prm.order;
-  for (int l = 0; l <= p; ++l) {
-    const float* e = (const float*)c->ringE + (int64_t)slots[l] * c->W;
-    const float* b = (const float*)c->ringB + (int64_t)slots[l] * c->W;
+  const int64_t start = (((s - p) % c->R) + c->R) % c->R;
+  a.ringE = (const float*)c->ringE;
+  a.ringB = (const float*)c->ringB;
+  a.lstride = c->W;
+  for (int l = 0; l <= p; ++l) {  // the same levels as per-level pointers
+    const float* e = (const float*)c->ringE + (start + l) * c->W;
+    const float* b = (const float*)c->ringB + (start + l) * c->W;
     if (prev) {
       a.Ep[l] = e;
       a.Bp[l] = b;
@@ -493,9 +529,11 @@ static void fill_mixed(pic_ctx* c, PushArgsMixed& a, const int* slots, int64_t l
     }
   }
   if (prev) {
+    a.start_prev = start;
     a.lo_p = (int32_t)lo;
     a.hi_p = (int32_t)hi;
   } else {
+    a.start_cur = start;
     a.lo = (int32_t)lo;
     a.hi = (int32_t)hi;
   }
@@ -579,16 +617,22 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
       e = launch_push_f64(a, p, c->stream, &launches);
     } else {
       PushArgsMixed a = base;
-      fill_mixed(c, a, slots, lo, hi, false);
+      fill_mixed(c, a, s, lo, hi, false);
+      // this step's fields at t_n on every window node, for the m = 1 pushes
+      e = launch_halfstep(a, p, W, c->half, c->half + W, c->stream);
+      ++launches;
+      if (e != cudaSuccess) return fail(c, PIC_ECUDA, "half-step launch: %s", cudaGetErrorString(e));
+      a.halfE = c->half;
+      a.halfB = c->half + W;
       if (binned) {
         const int64_t qsz = 7 * c->capacity;
         if (j > 0) {
           int ps[kMaxOrder + 1];
           int64_t plo, phi;
           step_slots(c, s - 1, ps, &plo, &phi);
-          fill_mixed(c, a, ps, plo, phi, true);
+          fill_mixed(c, a, s - 1, plo, phi, true);
         } else {
-          fill_mixed(c, a, slots, lo, hi, true);  // no deferred work on the first step
+          fill_mixed(c, a, s, lo, hi, true);  // no deferred work on the first step
         }
         a.queue_in = c->queue + (j & 1) * qsz;
         a.queue_out = c->queue + ((j + 1) & 1) * qsz;
@@ -604,7 +648,7 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
           int64_t plo, phi;
           if (j % c->predict_every == 0 && step_slots(c, s - 1, ps, &plo, &phi) == PIC_OK) {
             PushArgsMixed fa = a;
-            fill_mixed(c, fa, ps, plo, phi, false);
+            fill_mixed(c, fa, s - 1, plo, phi, false);
             e = launch_features_mixed(fa, p, c->phi, c->stream);
             if (e == cudaSuccess)
               e = launch_mlp_infer(mlp_device_params(c->mlp), c->phi, c->n, c->pred, c->sm_count,
@@ -623,7 +667,7 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
         if (e == cudaSuccess && j == n_steps - 1) {
           // close the call: finish what the last step deferred, public status bytes
           PushArgsMixed f = a;
-          fill_mixed(c, f, slots, lo, hi, true);
+          fill_mixed(c, f, s, lo, hi, true);
           f.queue_in = c->queue + (n_steps & 1) * qsz;
           f.qcount_in = c->qcount + (n_steps & 1) * 8;
           f.queue_out = c->queue + ((n_steps + 1) & 1) * qsz;
@@ -658,7 +702,7 @@ extern "C" int pic_features(pic_ctx* c, int64_t n, float* phi) {
   a.cell = c->cell; a.frac = c->frac; a.px = c->fpx; a.py = c->fpy; a.pz = c->fpz;
   a.status = c->status;
   a.mask = (int32_t)(c->W - 1);
-  fill_mixed(c, a, slots, lo, hi, false);
+  fill_mixed(c, a, n, lo, hi, false);
   CUDA_TRY(c, launch_features_mixed(a, c->prm.order, phi, c->stream));
   ++c->launches;
   return PIC_OK;

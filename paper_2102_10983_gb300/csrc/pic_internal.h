@@ -59,10 +59,22 @@ struct PushArgsMixed {
   float* py;
   float* pz;
   uint8_t* status;
+  // fields, ring form (ringE != nullptr): a mirrored ring of 2R slots of lstride
+  // floats, every level stored in slot (level mod R) and in that slot + R, so a
+  // step's p+1 levels are consecutive from slot start_cur (previous step:
+  // start_prev).  Pointer form (ringE == nullptr): one pointer per level.
+  const float* ringE;
+  const float* ringB;
+  int64_t lstride;
+  int64_t start_cur, start_prev;
   const float* E[kMaxOrder + 1];   // this step's levels n-p .. n
   const float* B[kMaxOrder + 1];
   const float* Ep[kMaxOrder + 1];  // previous step's levels (binned: deferred work)
   const float* Bp[kMaxOrder + 1];
+  // E_y and B_z of every window node interpolated to t_n (theta = 1/2), written
+  // by the step's half-step kernel; nullptr = not provided (gather the levels)
+  const float* halfE;
+  const float* halfB;
   int32_t lo, hi;      // tent node j must satisfy lo <= j and j+1 <= hi
   int32_t lo_p, hi_p;  // same for the previous step
   int32_t mask;
@@ -98,6 +110,60 @@ void lagrange_monomials(int p, float (&mono)[2][kMaxOrder + 1][kMaxOrder + 1]);
 // Sets the reason pic_last_error(NULL) reports.
 void set_global_error(const char* msg);
 
+// One ensemble of a batch, as the batched kernel reads it.
+struct EnsDev {
+  float dt, psi_max, qm, qm_abs, inv_dx;
+  int32_t k_max, field_time, pad;
+  const float* ringE;  // mirrored ring of this ensemble (2R slots x W)
+  const float* ringB;
+  const int64_t* slot_i0;  // [R] window origin of each ring slot
+  int64_t first, count;    // particle range in the concatenated store
+  int64_t chunk_first;     // index of its first stream chunk
+};
+
+// Arguments of one batched macro step.
+struct BatchArgs {
+  int32_t n_ens;
+  const EnsDev* ens;
+  int64_t n_total, n_chunks;
+  int32_t chunk;  // particles per stream chunk (multiple of 32)
+  int32_t* cell;
+  float* frac;
+  float* px;
+  float* py;
+  float* pz;
+  uint8_t* status;
+  int64_t R, lstride;  // ring slots, W
+  int32_t mask;
+  int64_t start_cur, start_prev;
+  const float* wtab;
+  int64_t crit_row;
+  float mono[2][kMaxOrder + 1][kMaxOrder + 1];
+  DevStats* stats;
+  const int32_t* queue_in;  // ensemble e, k: entries from 7*first_e + (k-1)*count_e
+  int32_t* queue_out;
+  int32_t* qcount_in;   // [n_ens][8]
+  int32_t* qcount_out;
+  const int64_t* prefix;  // [7*n_ens + 1] heavy-item prefix (filled per launch)
+  float* half;            // [2][n_ens][W]: E_y, B_z of every node at t_n (filled per launch)
+  int* cursor;
+  unsigned* blocks_done;
+  int parity_cur, parity_next, finalize;
+};
+
+cudaError_t launch_batch_step(const BatchArgs& a, int order, int blocks, cudaStream_t s,
+                              int* launches);
+int batch_max_blocks_per_sm(int order);
+cudaError_t launch_batch_scatter(const EnsDev* ens, int32_t n_ens, int64_t slot, int64_t R,
+                                 int64_t W, const double* Ey, const double* Bz, const int64_t* i0,
+                                 int64_t* slot_i0_all, cudaStream_t s);
+cudaError_t launch_to_mixed(const double* x, const double* px, const double* py, const double* pz,
+                            int32_t* cell, float* frac, float* fpx, float* fpy, float* fpz,
+                            double inv_dx, int64_t n, cudaStream_t s);
+cudaError_t launch_from_mixed(const int32_t* cell, const float* frac, const float* fpx,
+                              const float* fpy, const float* fpz, double* x, double* px, double* py,
+                              double* pz, double dx, int64_t n, cudaStream_t s);
+
 // Launchers (return cudaError_t of the launch).
 cudaError_t build_wtab_f64(double* wtab, int order, int k_max, int field_time, cudaStream_t s);
 cudaError_t build_wtab_f32(float* wtab, const double* wtab64, int64_t count, cudaStream_t s);
@@ -108,6 +174,9 @@ cudaError_t launch_push_mixed(const PushArgsMixed& a, int order, int schedule, i
 // call (the last step's deferred particles, then public status bytes).
 cudaError_t launch_binned_step(const PushArgsMixed& a, int order, int sm_count, cudaStream_t main,
                                int* launches);
+// E_y, B_z of every window node at t_n (the theta = 1/2 weights of a's step).
+cudaError_t launch_halfstep(const PushArgsMixed& a, int order, int64_t W, float* outE, float* outB,
+                            cudaStream_t s);
 cudaError_t launch_features_mixed(const PushArgsMixed& a, int order, float* phi, cudaStream_t s);
 
 cudaError_t launch_bin_predicted(const uint8_t* pred, uint8_t* status, int64_t n, int parity_cur,

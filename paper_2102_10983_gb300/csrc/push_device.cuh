@@ -1,0 +1,501 @@
+// Per-particle device arithmetic of the mixed-precision push, shared by the
+// single-problem kernels (push_mixed.cu) and the batched kernel (push_batch.cu).
+// Included in namespace pic by those translation units only.
+#pragma once
+
+#include <limits.h>
+#include <math.h>
+
+#include "pic_internal.h"
+
+namespace pic {
+
+// ---------------------------------------------------------------- per-particle math
+
+// The p+1 levels of one grid used by one macro step (level 0 = oldest).
+// Ring form: consecutive slots of the mirrored ring, level l at base + l*W.
+// Pointer form: one pointer per level (levels owned by the caller).
+template <int P, bool RING>
+struct Levels;
+template <int P>
+struct Levels<P, true> {
+  const float* base;
+  int32_t lstride;  // l * lstride + node stays below 2^31 (window <= 2^28 nodes)
+  __device__ __forceinline__ const float* at(int l) const { return base + (uint32_t)(l * lstride); }
+};
+template <int P>
+struct Levels<P, false> {
+  const float* ptr[P + 1];
+  __device__ __forceinline__ const float* at(int l) const { return ptr[l]; }
+};
+
+// Temporal sums at the two tent nodes jn, jn+1, then the tent weight wt.
+template <int P, class LV>
+__device__ __forceinline__ float gather_f32(const LV& lv, const float* w, int32_t jn, float wt,
+                                            int32_t mask) {
+  const int32_t a0 = jn & mask, a1 = (jn + 1) & mask;
+  float f0 = __fmul_rn(w[0], __ldg(lv.at(0) + a0));
+  float f1 = __fmul_rn(w[0], __ldg(lv.at(0) + a1));
+#pragma unroll
+  for (int l = 1; l <= P; ++l) {
+    f0 = __fmaf_rn(w[l], __ldg(lv.at(l) + a0), f0);
+    f1 = __fmaf_rn(w[l], __ldg(lv.at(l) + a1), f1);
+  }
+  return __fmaf_rn(wt, __fsub_rn(f1, f0), f0);
+}
+
+struct MixedState {
+  int32_t cell;
+  float frac, ux, uy, uz;
+};
+
+// Tent coordinates of offset f from node `cell`: E grid nodes at i dx, B grid
+// nodes at (i + 1/2) dx.  False if a node is outside [lo, hi].
+__device__ __forceinline__ bool tent_coords(int32_t cell, float f, int32_t lo, int32_t hi,
+                                            int32_t& je, float& we, int32_t& jb, float& wb) {
+  const float fe = floorf(f);
+  const float fbm = __fsub_rn(f, 0.5f);
+  const float fb = floorf(fbm);
+  je = cell + (int32_t)fe;
+  we = __fsub_rn(f, fe);
+  jb = cell + (int32_t)fb;
+  wb = __fsub_rn(fbm, fb);
+  return je >= lo && je < hi && jb >= lo && jb < hi;
+}
+
+__device__ __forceinline__ float norm2(float a, float b, float c) {
+  return __fmaf_rn(c, c, __fmaf_rn(b, b, __fmul_rn(a, a)));
+}
+
+// Criterion (Sec. IV) in FP32: Psi0 = |q/m| |B| dt / (2 gamma); smallest k with
+// Psi0 / 4^k <= Psi_max, capped at k_max.
+__device__ __forceinline__ int psi_to_k(float b0, const MixedState& s, float qm_abs, float dt,
+                                        float psi_max, int k_max, bool& capped) {
+  const float g0 = __fsqrt_rn(__fadd_rn(1.0f, norm2(s.ux, s.uy, s.uz)));
+  float psi = __fdiv_rn(__fmul_rn(__fmul_rn(qm_abs, fabsf(b0)), dt), __fmul_rn(2.0f, g0));
+  int k = 0;
+  while (psi > psi_max && k < k_max) {
+    psi = __fmul_rn(psi, 0.25f);
+    ++k;
+  }
+  capped = psi > psi_max;
+  return k;
+}
+
+// b0 is B_z at the particle and t_n: with m = 1 it is also the first (and only)
+// sub-step's B_z, since both use the theta = 1/2 weights at the same nodes.
+template <int P, class LV>
+__device__ __forceinline__ int criterion_f32(const LV& B, const float* wcrit, int32_t jb,
+                                             float wb, int32_t mask, const MixedState& s,
+                                             float qm_abs, float dt, float psi_max, int k_max,
+                                             bool& capped, float& b0) {
+  b0 = gather_f32<P>(B, wcrit, jb, wb, mask);
+  return psi_to_k(b0, s, qm_abs, dt, psi_max, k_max, capped);
+}
+
+// Field view of one macro step.
+template <int P, bool RING>
+struct StepFields {
+  Levels<P, RING> E, B;
+  int32_t lo, hi;
+};
+
+// One Boris sub-step (Eqs. eq:p - eq:gamman) and the position update (Eq. eq:x)
+// in the fields ey, bz, with momentum step hp and offset step hx (cells per
+// unit velocity).
+__device__ __forceinline__ void boris_f32(float ey, float bz, float hp, float hx, float qm,
+                                          MixedState& s) {
+  const float half = __fmul_rn(0.5f, hp);
+  const float dpy = __fmul_rn(__fmul_rn(qm, ey), half);
+  const float mx = s.ux, my = __fadd_rn(s.uy, dpy), mz = s.uz;
+  const float inv_gn = rsqrtf(__fadd_rn(1.0f, norm2(mx, my, mz)));
+  const float tz = __fmul_rn(__fmul_rn(__fmul_rn(qm, bz), half), inv_gn);
+  const float ppx = __fmaf_rn(my, tz, mx);
+  const float ppy = __fmaf_rn(-mx, tz, my);
+  const float sz = __fdividef(__fmul_rn(2.0f, tz), __fmaf_rn(tz, tz, 1.0f));
+  s.ux = __fmaf_rn(ppy, sz, mx);
+  s.uy = __fadd_rn(__fmaf_rn(-ppx, sz, my), dpy);
+  s.uz = mz;
+  const float inv_g = rsqrtf(__fadd_rn(1.0f, norm2(s.ux, s.uy, s.uz)));
+  s.frac = __fmaf_rn(hx, __fmul_rn(s.ux, inv_g), s.frac);
+}
+
+// Reciprocal of prod_{k != j} (j - k), the denominator of L_{p,j} (Sec. VI).
+__host__ __device__ constexpr float lagrange_inv_den(int p, int j) {
+  float d = 1.f;
+  for (int k = 0; k <= p; ++k)
+    if (k != j) d *= (float)(j - k);
+  return 1.f / d;
+}
+
+// Weights of Eqs. eq:lagrange2-3 (E) and eq:lagrange2-2 (B) at theta, in FP32:
+// prod_{k != j} (c_k + theta) times the reciprocal denominator, c_k = p-k-1/2
+// (E) or p-k-1 (B).  Depends on the sub-step index only, so these FP32 ops run
+// alongside the serial chain of the push instead of on it.
+template <int P>
+__device__ __forceinline__ void lagrange_f32(float theta, float* w) {
+#pragma unroll
+  for (int j = 0; j <= P; ++j) {
+    float ne = 1.f, nb = 1.f;
+#pragma unroll
+    for (int k = 0; k <= P; ++k) {
+      if (k == j) continue;
+      ne = __fmul_rn(ne, __fadd_rn((float)(P - k) - 0.5f, theta));
+      nb = __fmul_rn(nb, __fadd_rn((float)(P - k) - 1.0f, theta));
+    }
+    w[j] = __fmul_rn(ne, lagrange_inv_den(P, j));
+    w[P + 1 + j] = __fmul_rn(nb, lagrange_inv_den(P, j));
+  }
+}
+
+// Temporal sum over the levels' values v at one node, then nothing else: the
+// same operation order as gather_f32.
+template <int P>
+__device__ __forceinline__ float tsum(const float* w, const float* v) {
+  float f = __fmul_rn(w[0], v[0]);
+#pragma unroll
+  for (int l = 1; l <= P; ++l) f = __fmaf_rn(w[l], v[l], f);
+  return f;
+}
+
+// The m = 4^k sub-steps of one macro step (Algorithm 1).  False if the particle
+// left the window (state kept as reached).
+//
+// Coefficients of the interpolating polynomial in u at two nodes a0, a1 of the
+// given levels: c_q = sum_l v_l M[l][q].
+template <int P, class LV>
+__device__ __forceinline__ void to_monomial(const LV& lv, int32_t a0, int32_t a1,
+                                            const float (&M)[kMaxOrder + 1][kMaxOrder + 1],
+                                            float* c0, float* c1) {
+  float v0[P + 1], v1[P + 1];
+#pragma unroll
+  for (int l = 0; l <= P; ++l) {
+    v0[l] = __ldg(lv.at(l) + a0);
+    v1[l] = __ldg(lv.at(l) + a1);
+  }
+#pragma unroll
+  for (int q = 0; q <= P; ++q) {
+    float x0 = __fmul_rn(v0[0], M[0][q]), x1 = __fmul_rn(v1[0], M[0][q]);
+#pragma unroll
+    for (int l = 1; l <= P; ++l) {
+      x0 = __fmaf_rn(v0[l], M[l][q], x0);
+      x1 = __fmaf_rn(v1[l], M[l][q], x1);
+    }
+    c0[q] = x0;
+    c1[q] = x1;
+  }
+}
+
+template <int P>
+__device__ __forceinline__ float horner(const float* c, float u) {
+  float f = c[P];
+#pragma unroll
+  for (int q = P - 1; q >= 0; --q) f = __fmaf_rn(f, u, c[q]);
+  return f;
+}
+
+// m = 1 takes a straight path with the tabulated weights and the criterion's
+// B_z (b0; unused for m > 1).  For m > 1 the
+// temporal interpolant at each tent node is a polynomial of degree p in
+// u = theta - 1; its coefficients are formed when the node index changes (an
+// electron moves a small fraction of a cell per sub-step) and each sub-step
+// evaluates it by Horner's rule: p FMAs per node, nothing waits on memory.
+template <int P, bool RING>
+__device__ __forceinline__ bool subcycle_f32(const StepFields<P, RING>& F, const float* wtab,
+                                             int32_t mask, float dt, float inv_dx, float qm,
+                                             int field_time,
+                                             const float (&mono)[2][kMaxOrder + 1][kMaxOrder + 1],
+                                             int k, int k_prev, float b0, MixedState& s) {
+  constexpr int stride = 2 * (P + 1);
+  const float h = ldexpf(dt, -2 * k);
+  const float h_old = ldexpf(dt, -2 * k_prev);
+  const float hx = __fmul_rn(h, inv_dx);
+  float hp = __fmul_rn(0.5f, __fadd_rn(h_old, h));
+  if (k == 0) {
+    const float* wr = wtab + wrow(0, 1) * stride;
+    int32_t je, jb;
+    float we, wb;
+    if (!tent_coords(s.cell, s.frac, F.lo, F.hi, je, we, jb, wb)) return false;
+    const float ey = gather_f32<P>(F.E, wr, je, we, mask);
+    boris_f32(ey, b0, hp, hx, qm, s);  // b0: the criterion's B_z (same weights, same nodes)
+    return true;
+  }
+  const int m = 1 << (2 * k);
+  const float inv_m = ldexpf(1.0f, -2 * k);
+  // u_j = theta_j - 1, exact in FP32 for m <= 4^7
+  const float u1 = field_time == 0 ? -0.5f : __fsub_rn(__fmul_rn(0.5f, inv_m), 1.0f);
+  int32_t ce = INT_MIN, cb = INT_MIN;
+  float ce0[P + 1], ce1[P + 1], cb0[P + 1], cb1[P + 1];  // monomial coefficients per node
+  for (int j = 1; j <= m; ++j) {
+    const float u = __fmaf_rn((float)(j - 1), inv_m, u1);
+    int32_t je, jb;
+    float we, wb;
+    if (!tent_coords(s.cell, s.frac, F.lo, F.hi, je, we, jb, wb)) return false;
+    if (je != ce) {
+      ce = je;
+      to_monomial<P>(F.E, je & mask, (je + 1) & mask, mono[0], ce0, ce1);
+    }
+    if (jb != cb) {
+      cb = jb;
+      to_monomial<P>(F.B, jb & mask, (jb + 1) & mask, mono[1], cb0, cb1);
+    }
+    const float fe0 = horner<P>(ce0, u), fe1 = horner<P>(ce1, u);
+    const float fb0 = horner<P>(cb0, u), fb1 = horner<P>(cb1, u);
+    const float ey = __fmaf_rn(we, __fsub_rn(fe1, fe0), fe0);
+    const float bz = __fmaf_rn(wb, __fsub_rn(fb1, fb0), fb0);
+    boris_f32(ey, bz, hp, hx, qm, s);
+    hp = h;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void normalize(MixedState& s) {
+  const float fl = floorf(s.frac);
+  s.cell += (int32_t)fl;
+  s.frac = __fsub_rn(s.frac, fl);
+}
+
+// ---------------------------------------------------------------- counters
+
+// Per-thread counters: k = 0 steps and sub-step sums in registers; rare events
+// (k > 0, caps, losses) straight into shared memory.
+struct ThreadCounters {
+  unsigned long long k0 = 0, sub = 0, star = 0;
+};
+
+__device__ __forceinline__ void count_step(ThreadCounters& tc, unsigned long long* sh, int k,
+                                           bool capped) {
+  const unsigned long long m = 1ull << (2 * k);
+  tc.sub += m;
+  if (k == 0) {
+    ++tc.k0;
+  } else {
+    tc.star += m;
+    atomicAdd(&sh[k], 1ull);
+  }
+  if (capped) atomicAdd(&sh[10], 1ull);
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// All threads of the block must call this.
+__device__ __forceinline__ void flush_counters(const ThreadCounters& tc, unsigned long long* sh,
+                                               DevStats* st) {
+  const unsigned long long k0 = warp_sum(tc.k0), sub = warp_sum(tc.sub), star = warp_sum(tc.star);
+  if ((threadIdx.x & 31) == 0) {
+    if (k0) atomicAdd(&sh[0], k0);
+    if (sub) atomicAdd(&sh[8], sub);
+    if (star) atomicAdd(&sh[9], star);
+  }
+  __syncthreads();
+  if (threadIdx.x < 12) {
+    const unsigned long long v = sh[threadIdx.x];
+    if (v) {
+      unsigned long long* dst = threadIdx.x < 8 ? &st->k_hist[threadIdx.x]
+                                : threadIdx.x == 8 ? &st->substeps
+                                : threadIdx.x == 9 ? &st->n_star
+                                : threadIdx.x == 10 ? &st->clamped
+                                                    : &st->lost;
+      atomicAdd(dst, v);
+    }
+  }
+}
+
+__device__ __forceinline__ MixedState load_state(const PushArgsMixed& a, int64_t i) {
+  MixedState s;
+  s.cell = a.cell[i];
+  s.frac = a.frac[i];
+  s.ux = a.px[i];
+  s.uy = a.py[i];
+  s.uz = a.pz[i];
+  return s;
+}
+
+__device__ __forceinline__ void store_state(const PushArgsMixed& a, int64_t i, const MixedState& s) {
+  a.cell[i] = s.cell;
+  a.frac[i] = s.frac;
+  a.px[i] = s.ux;
+  a.py[i] = s.uy;
+  a.pz[i] = s.uz;
+}
+
+// The current (prev = false) or previous step's field view from the launch
+// arguments: ring form from the mirrored ring's start slot, pointer form from
+// the per-level pointers.
+template <int P, bool RING>
+__device__ __forceinline__ void load_fields(StepFields<P, RING>& F, const PushArgsMixed& a,
+                                            bool prev) {
+  if constexpr (RING) {
+    const int64_t start = prev ? a.start_prev : a.start_cur;
+    F.E.base = a.ringE + start * a.lstride;
+    F.B.base = a.ringB + start * a.lstride;
+    F.E.lstride = a.lstride;
+    F.B.lstride = a.lstride;
+  } else {
+#pragma unroll
+    for (int l = 0; l <= P; ++l) {
+      F.E.ptr[l] = prev ? a.Ep[l] : a.E[l];
+      F.B.ptr[l] = prev ? a.Bp[l] : a.B[l];
+    }
+  }
+  F.lo = prev ? a.lo_p : a.lo;
+  F.hi = prev ? a.hi_p : a.hi;
+}
+
+// ---------------------------------------------------------------- binned schedule pieces
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kChunk = 256;          // particles per stream item (8 per lane)
+constexpr int kDeferMin = 3;         // smallest k that is deferred
+constexpr int kStashK = kDeferMin - 1;
+constexpr int kStashCap = 64;
+constexpr uint8_t kParity = 0x08;
+constexpr uint8_t kDeferMask = 0x70;
+
+__device__ __forceinline__ int deferred_k(uint8_t st) { return (st >> 4) & 7; }
+
+// Enqueue particle i into the queue of its k; warp-aggregated: one atomic per
+// distinct k in the warp.  All 32 lanes call this; key 0 = nothing.
+__device__ __forceinline__ void enqueue(const PushArgsMixed& a, int key, int32_t i) {
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  int base = 0;
+  if (key != 0 && lane == leader) base = atomicAdd(&a.qcount_out[key], __popc(peers));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (key != 0) {
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    a.queue_out[(int64_t)(key - 1) * a.qcap + base + rank] = i;
+  }
+}
+
+// A warp's stash of particles waiting for a short sub-cycle of one k.
+struct Stash {
+  int32_t idx[kStashCap];
+  int32_t cell[kStashCap];
+  float frac[kStashCap], ux[kStashCap], uy[kStashCap], uz[kStashCap];
+  uint8_t kp[kStashCap];
+};
+
+// Push the first `cnt` (<= 32) stashed particles, one per lane, with 4^k
+// sub-steps each; then move entries [cnt, n) to the front.  Warp-collective.
+template <int P, bool RING>
+__device__ __forceinline__ void stash_drain(const PushArgsMixed& a, const StepFields<P, RING>& F,
+                                            Stash& S, int k, int& n, int cnt,
+                                            unsigned long long* sh) {
+  const int lane = threadIdx.x & 31;
+  if (lane < cnt) {
+    MixedState s = {S.cell[lane], S.frac[lane], S.ux[lane], S.uy[lane], S.uz[lane]};
+    const int32_t i = S.idx[lane];
+    const bool ok = subcycle_f32<P>(F, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, a.field_time, a.mono,
+                                    k, S.kp[lane], 0.f, s);
+    normalize(s);
+    store_state(a, i, s);
+    a.status[i] = ok ? (uint8_t)(k | (a.parity_next ? kParity : 0)) : (uint8_t)(k | PIC_STATUS_LOST);
+    if (!ok) atomicAdd(&sh[11], 1ull);
+  }
+  __syncwarp();
+  const int rest = n - cnt;
+  if (lane < rest) {
+    const int q = cnt + lane;
+    S.idx[lane] = S.idx[q];
+    S.cell[lane] = S.cell[q];
+    S.frac[lane] = S.frac[q];
+    S.ux[lane] = S.ux[q];
+    S.uy[lane] = S.uy[q];
+    S.uz[lane] = S.uz[q];
+    S.kp[lane] = S.kp[q];
+  }
+  __syncwarp();
+  n = rest;
+}
+
+// Deferred item: finish the previous step of particle i, then take its
+// criterion for the current step (pushed at once if k < kDeferMin, else
+// deferred again).  finalize: only finish the deferred step (public status).
+template <int P, bool RING>
+__device__ __forceinline__ void heavy_particle(const PushArgsMixed& a, const StepFields<P, RING>& Fp,
+                                               const StepFields<P, RING>& Fc, const float* wcrit,
+                                               int64_t i, ThreadCounters& tc,
+                                               unsigned long long* sh, int& defer_key) {
+  defer_key = 0;
+  const uint8_t st = a.status[i];
+  const int k = deferred_k(st);
+  const int k_prev = st & 7;
+  MixedState s = load_state(a, i);
+  const bool ok = subcycle_f32<P>(Fp, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, a.field_time, a.mono,
+                                  k, k_prev, 0.f, s);
+  normalize(s);
+  if (!ok) {
+    store_state(a, i, s);
+    a.status[i] = (uint8_t)(k | PIC_STATUS_LOST);
+    atomicAdd(&sh[11], 1ull);
+    return;
+  }
+  if (a.finalize) {
+    store_state(a, i, s);
+    a.status[i] = (uint8_t)k;
+    return;
+  }
+  int32_t je, jb;
+  float we, wb;
+  if (!tent_coords(s.cell, s.frac, Fc.lo, Fc.hi, je, we, jb, wb)) {
+    store_state(a, i, s);
+    a.status[i] = (uint8_t)(k | PIC_STATUS_LOST);
+    atomicAdd(&sh[11], 1ull);
+    return;
+  }
+  bool capped;
+  float b0;
+  const int kn = criterion_f32<P>(Fc.B, wcrit, jb, wb, a.mask, s, a.qm_abs, a.dt, a.psi_max,
+                                  a.k_max, capped, b0);
+  count_step(tc, sh, kn, capped);
+  if (kn < kDeferMin) {
+    const bool ok2 = subcycle_f32<P>(Fc, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, a.field_time,
+                                     a.mono, kn, k, b0, s);
+    normalize(s);
+    store_state(a, i, s);
+    a.status[i] = ok2 ? (uint8_t)(kn | (a.parity_next ? kParity : 0)) : (uint8_t)(kn | PIC_STATUS_LOST);
+    if (!ok2) atomicAdd(&sh[11], 1ull);
+  } else {
+    store_state(a, i, s);
+    a.status[i] = (uint8_t)(k | (kn << 4));
+    defer_key = kn;
+  }
+}
+
+// Predicted item: particle i was binned before the launch as likely to
+// sub-cycle; take its exact criterion and all its sub-steps now.
+template <int P, bool RING>
+__device__ __forceinline__ void predicted_particle(const PushArgsMixed& a, const StepFields<P, RING>& Fc,
+                                                   const float* wcrit, int64_t i, ThreadCounters& tc,
+                                                   unsigned long long* sh) {
+  const uint8_t st = a.status[i];
+  const int k_prev = st & 7;
+  MixedState s = load_state(a, i);
+  int32_t je, jb;
+  float we, wb;
+  if (!tent_coords(s.cell, s.frac, Fc.lo, Fc.hi, je, we, jb, wb)) {
+    a.status[i] = (uint8_t)(k_prev | PIC_STATUS_LOST);
+    atomicAdd(&sh[11], 1ull);
+    return;
+  }
+  bool capped;
+  float b0;
+  const int k = criterion_f32<P>(Fc.B, wcrit, jb, wb, a.mask, s, a.qm_abs, a.dt, a.psi_max,
+                                 a.k_max, capped, b0);
+  count_step(tc, sh, k, capped);
+  const bool ok = subcycle_f32<P>(Fc, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, a.field_time, a.mono,
+                                  k, k_prev, b0, s);
+  normalize(s);
+  store_state(a, i, s);
+  a.status[i] = ok ? (uint8_t)(k | (a.parity_next ? kParity : 0)) : (uint8_t)(k | PIC_STATUS_LOST);
+  if (!ok) atomicAdd(&sh[11], 1ull);
+}
+
+}  // namespace pic

@@ -32,6 +32,12 @@ class PicParams(ctypes.Structure):
                 ("schedule", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
+class PicEnsemble(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("dx", ctypes.c_double), ("psi_max", ctypes.c_double),
+                ("qm", ctypes.c_double), ("k_max", ctypes.c_int32), ("field_time", ctypes.c_int32),
+                ("n_particles", ctypes.c_int64)]
+
+
 class PicStepStats(ctypes.Structure):
     _fields_ = [("k_hist", ctypes.c_int64 * 8), ("substeps", ctypes.c_int64),
                 ("n_star", ctypes.c_int64), ("clamped", ctypes.c_int64),
@@ -68,6 +74,19 @@ SIGNATURES = {
     "pic_mlp_grad": (ctypes.c_int, [_VP, _VP, _VP, _I64, _VP, _VP]),
     "pic_mlp_train_step": (ctypes.c_int, [_VP, _VP, _VP, _I64, ctypes.c_float, _VP]),
     "pic_mlp_infer": (ctypes.c_int, [_VP, _VP, _I64, _VP]),
+    "pic_batch_create": (ctypes.c_int, [ctypes.POINTER(PicEnsemble), _I32, _I32, _I64, _I32, _VP,
+                                        ctypes.POINTER(_VP)]),
+    "pic_batch_destroy": (ctypes.c_int, [_VP]),
+    "pic_batch_config": (ctypes.c_int, [_VP, _I32, _I32, _I32]),
+    "pic_batch_particles_write": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _I32]),
+    "pic_batch_particles_read": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _I32]),
+    "pic_batch_fields_upload": (ctypes.c_int, [_VP, _I64, _VP, _VP, _VP, _I32]),
+    "pic_batch_push_step": (ctypes.c_int, [_VP, _I64, _I64, ctypes.POINTER(PicStepStats)]),
+    "pic_batch_timing": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
+    "pic_batch_launch_count": (ctypes.c_int64, [_VP]),
+    "pic_batch_autotune": (ctypes.c_int, [_VP, _I64, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                                          ctypes.POINTER(_D)]),
+    "pic_batch_last_error": (ctypes.c_char_p, [_VP]),
     "pic_push_mixed_noalloc": (ctypes.c_int, [ctypes.POINTER(PicParams), _I64, _VP, _VP, _VP, _VP,
                                               _VP, _VP, _VP, _VP, _VP, _I64, _I64, _I64, _VP,
                                               ctypes.POINTER(PicStepStats)]),
@@ -293,3 +312,81 @@ def unpack_params(buf) -> dict:
         out[name] = buf[off:off + size].reshape(shape)
         off += size
     return out
+
+
+class Batch:
+    """Batched ensembles (pic_batch_*): arrays are concatenated in ensemble order."""
+
+    def __init__(self, ensembles, order=3, window=512, ring_levels=None, stream=None):
+        arr = (PicEnsemble * len(ensembles))()
+        for q, e in enumerate(ensembles):
+            arr[q] = PicEnsemble(float(e["dt"]), float(e["dx"]), float(e["psi_max"]),
+                                 float(e.get("qm", -1.0)), int(e.get("k_max", 7)),
+                                 int(e.get("field_time", 0)), int(e["n_particles"]))
+        self.n_ens = len(ensembles)
+        self.counts = [int(e["n_particles"]) for e in ensembles]
+        self.n_total = sum(self.counts)
+        self.window = int(window)
+        self.order = int(order)
+        self.ring_levels = int(ring_levels if ring_levels is not None else order + 2)
+        h = ctypes.c_void_p()
+        code = lib().pic_batch_create(arr, self.n_ens, self.order, self.window, self.ring_levels,
+                                      _stream_handle(stream), ctypes.byref(h))
+        _check(code)
+        self.h = h
+
+    def _chk(self, code, ok=(PIC_OK,)):
+        if code not in ok:
+            raise PicError(code, (lib().pic_batch_last_error(self.h) or b"").decode())
+        return code
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pic_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def config(self, chunk=256, blocks_per_sm=2, use_graph=False):
+        self._chk(lib().pic_batch_config(self.h, int(chunk), int(blocks_per_sm), 1 if use_graph else 0))
+
+    def particles_write(self, x, px, py, pz, status=None):
+        w = _where(x, px, py, pz, status)
+        self._chk(lib().pic_batch_particles_write(self.h, _ptr(x)[0], _ptr(px)[0], _ptr(py)[0],
+                                                  _ptr(pz)[0], _ptr(status)[0], w))
+
+    def read_numpy(self):
+        out = [np.empty(self.n_total) for _ in range(4)] + [np.empty(self.n_total, np.uint8)]
+        self._chk(lib().pic_batch_particles_read(self.h, *[o.ctypes.data for o in out], PIC_HOST))
+        return out
+
+    def fields_upload(self, level, i0, Ey, Bz):
+        i0 = np.ascontiguousarray(i0, dtype=np.int64)
+        w = _where(Ey, Bz)
+        self._chk(lib().pic_batch_fields_upload(self.h, int(level), i0.ctypes.data, _ptr(Ey)[0],
+                                                _ptr(Bz)[0], w))
+
+    def push_step(self, n, n_steps=1, want_stats=True, ok=(PIC_OK, PIC_ERANGE, PIC_EKMAX)):
+        st = PicStepStats() if want_stats else None
+        code = lib().pic_batch_push_step(self.h, int(n), int(n_steps),
+                                         ctypes.byref(st) if st is not None else None)
+        self._chk(code, ok=ok)
+        return st
+
+    def timing(self, on=True):
+        ms, steps = ctypes.c_double(), ctypes.c_int64()
+        self._chk(lib().pic_batch_timing(self.h, 1 if on else 0, ctypes.byref(ms), ctypes.byref(steps)))
+        return ms.value, steps.value
+
+    def launches(self) -> int:
+        return int(lib().pic_batch_launch_count(self.h))
+
+    def autotune(self, n, steps=4):
+        c, b, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        self._chk(lib().pic_batch_autotune(self.h, int(n), int(steps), ctypes.byref(c),
+                                           ctypes.byref(b), ctypes.byref(ms)))
+        return c.value, b.value, ms.value

@@ -101,18 +101,25 @@ class ParticleInit:
         return int(self.x.shape[0])
 
 
-def electrons_at_rest(n: int, seed: int, x_lo: float, x_hi: float) -> ParticleInit:
+def electrons_at_rest(n: int, seed: int, x_lo: float, x_hi: float,
+                      sort_x: bool = False) -> ParticleInit:
     rng = np.random.Generator(np.random.PCG64(seed))
     x = rng.uniform(x_lo, x_hi, size=n)
+    if sort_x:
+        x = np.sort(x)
     z = np.zeros(n, dtype=np.float64)
     return ParticleInit(x, z.copy(), z.copy(), z.copy())
 
 
 def electrons_maxwellian(n: int, seed: int, x_lo: float, x_hi: float,
-                         sigma: float = MAXWELL_10KEV_SIGMA) -> ParticleInit:
-    """Non-relativistic Maxwellian: each momentum component N(0, sigma^2)."""
+                         sigma: float = MAXWELL_10KEV_SIGMA, sort_x: bool = False) -> ParticleInit:
+    """Non-relativistic Maxwellian: each momentum component N(0, sigma^2).
+    sort_x stores the electrons in order of initial position (the momenta stay
+    independent draws): a layout choice, the ensemble is the same."""
     rng = np.random.Generator(np.random.PCG64(seed))
     x = rng.uniform(x_lo, x_hi, size=n)
+    if sort_x:
+        x = np.sort(x)
     p = rng.standard_normal(size=(3, n)) * sigma
     return ParticleInit(x, p[0].copy(), p[1].copy(), p[2].copy())
 
@@ -138,6 +145,7 @@ class Workload:
     profile: str = "sine"
     xi0: float = 0.0
     sigma: float = 1.0
+    sort_x: bool = False            # store electrons in order of initial position
 
     @property
     def wave(self) -> PlaneWave:
@@ -146,8 +154,9 @@ class Workload:
     def particles(self, n: int | None = None) -> ParticleInit:
         n = self.n_particles if n is None else n
         if self.thermal_sigma > 0.0:
-            return electrons_maxwellian(n, self.seed, self.x_lo, self.x_hi, self.thermal_sigma)
-        return electrons_at_rest(n, self.seed, self.x_lo, self.x_hi)
+            return electrons_maxwellian(n, self.seed, self.x_lo, self.x_hi, self.thermal_sigma,
+                                        self.sort_x)
+        return electrons_at_rest(n, self.seed, self.x_lo, self.x_hi, self.sort_x)
 
     def origins(self, n_first: int, n_count: int) -> np.ndarray:
         if self.window_origin is not None:
@@ -180,4 +189,4 @@ C1 = Workload(name="c1_testparticle_a0_100", n_particles=256, a0=100.0, dt=DT75,
 C2 = Workload(name="c2_maxwellian_a0_150_16M", n_particles=16_777_216, a0=150.0, dt=DT75,
               dx=DT75 / 0.99, psi_max=0.01, order=3, n_steps=20_000,
               x_lo=0.0, x_hi=64 * TWO_PI, thermal_sigma=MAXWELL_10KEV_SIGMA, seed=2,
-              window=32768, window_origin=-512)
+              window=32768, window_origin=-512, sort_x=True)
