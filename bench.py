@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--acc-particles", type=int, default=524288)
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--predict-every", type=int, default=16)
     ap.add_argument("--batched-steps", type=int, default=200)
     ap.add_argument("--batched-ensembles", type=int, default=512)
     ap.add_argument("--cpu-sample", type=int, default=16384)
@@ -396,6 +398,11 @@ def run_ours(args, ws, rank, local):
                kern_ms=kern_ms / max(kern_steps, 1), stats=st.as_dict(),
                substeps_per_s=st.substeps * ws / (total_ms / 1e3))
 
+    # ---- the learned schedule: the predictor trained on pairs the integrator
+    #      logs from an at-rest a0 = 100 run, then the same timed window
+    if not args.no_learned:
+        out["learned"] = run_learned(args, make, start, Wu, K, last, n_e, ws, stream)
+
     # ---- the plain FP64 push from the same state (the mixed state at the start of
     #      the timed window, widened to FP64), K64 steps
     K64 = min(K, args.fp64_steps)
@@ -467,6 +474,63 @@ def run_ours(args, ws, rank, local):
     if not args.no_batched:
         out["batched"] = run_batched(args, dev, stream)
     return wl, out
+
+
+def run_learned(args, make, start, Wu, K, last, n_e, ws, stream):
+    import torch
+    from paper_2102_10983_gb300 import native, predictor
+    t0 = time.perf_counter()
+    X, Y, K0 = predictor.c1_style_training_set()
+    n_tr = int(0.9 * len(Y))
+    net = native.Predictor(seed=1)
+    losses = predictor.train(net, X[:n_tr], Y[:n_tr], iters=400)
+    pred = torch.empty(len(Y) - n_tr, dtype=torch.uint8, device=X.device)
+    net.infer(X[n_tr:].contiguous(), pred)
+    acc = float((pred == Y[n_tr:]).float().mean())
+    acc_prev = float((K0[n_tr:] == Y[n_tr:]).float().mean())
+    heavy = Y[n_tr:] >= 3
+    heavy_recall = float((pred[heavy] >= 3).float().mean()) if bool(heavy.any()) else None
+    false_alarm = float((pred[~heavy] >= 3).float().mean())
+    train_s = time.perf_counter() - t0
+    integ = make(native.PIC_MIXED, native.PIC_SCHED_PREDICTED, last)
+    integ.attach_predictor(net, args.predict_every)
+    if start > 0:
+        integ.pic_push_step(0, start, want_stats=False)
+    integ.pic_push_step(start, Wu, want_stats=False)
+    # what the network predicts for the first timed step, beside what the criterion takes
+    pred0 = torch.empty(n_e, dtype=torch.uint8, device="cuda")
+    native.predict(integ, net, start + Wu - 1, pred0)
+    pred_hist = torch.bincount(pred0.long(), minlength=8).tolist()
+    del pred0
+    torch.cuda.synchronize()
+    integ.timing(True)
+    launches0 = integ.launches()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    barrier(ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    integ.pic_push_step(start + Wu, K, want_stats=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    ms = max_over_ranks(ws, e0.elapsed_time(e1))
+    launches = integ.launches() - launches0
+    kern_ms, kern_steps = integ.timing_read()
+    integ.close()
+    net.close()
+    return {"value": aggregate_value(n_e, K, ws, ms), "ms_per_step": ms / K,
+            "kern_ms": kern_ms / max(kern_steps, 1), "clocks": clk,
+            "predict_every": args.predict_every, "gpu_launches": launches,
+            "predicted_k_hist_first_step": pred_hist,
+            "training": {"pairs": int(len(Y)), "held_out_accuracy": acc,
+                         "same_k_as_last_step_accuracy": acc_prev,
+                         "k_ge_3_recall": heavy_recall, "k_ge_3_false_alarm_rate": false_alarm,
+                         "loss_first_last": [losses[0], losses[-1]], "seconds": train_s,
+                         "data": "features after step n and k of step n+1, logged by the integrator "
+                                 "on 65,536 at-rest electrons in a0 = 100, lambda/75, 400 steps "
+                                 "(every pair kept: natural class frequencies)"}}
 
 
 def cpu_baseline(wl: W.Workload, n_sample: int, steps: int):
@@ -546,29 +610,37 @@ def main():
     # algorithmic bytes of the mixed push per particle-step: cell i32 + frac f32 +
     # p 3 x f32 + status u8, read and written
     bytes_per = 2 * (4 + 4 + 12 + 1)
-    achieved = bytes_per * wl.n_particles / (out["kern_ms"] / 1e3) / 1e9
+    kern_ms = out["learned"]["kern_ms"] if "learned" in out else out["kern_ms"]
+    achieved = bytes_per * wl.n_particles / (kern_ms / 1e3) / 1e9
+    headline = out.get("learned", {"value": out["value"], "ms_per_step": out["ms_per_step"]})
     line = {
-        "metric": METRIC, "value": out["value"], "unit": UNIT, "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["ms_per_step"],
+        "metric": METRIC, "value": headline["value"], "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": headline["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": wl.name, "electrons_per_gpu": wl.n_particles, "a0": wl.a0,
                    "dt": "lambda/75", "c_dt_over_dx": 0.99, "psi_max": wl.psi_max,
-                   "order": wl.order, "form": "mixed", "schedule": args.schedule,
+                   "order": wl.order, "form": "mixed",
+                   "schedule": "predicted (learned)" if "learned" in out else args.schedule,
                    "start_step": args.start_step,
                    "l2": "inputs larger than L2 (352 MB particle state per GPU)",
                    "layout": "electrons stored in order of initial position, never re-sorted",
                    "parallelism": f"replicas x{ws}"},
         "substeps_per_s": out["substeps_per_s"],
+        "exact_binned": {"value": out["value"], "ms_per_step": out["ms_per_step"],
+                         "note": "same form, electrons binned by the exact criterion only"},
+        "learned": out.get("learned"),
         "fp64_value": out.get("fp64_value"), "fp64_steps": out.get("fp64_steps"),
         "fp64_note": "plain FP64 push, same workload and steps, started from the timed window's state",
-        "speedup_vs_fp64": (out["value"] / out["fp64_value"]) if out.get("fp64_value") else None,
+        "speedup_vs_fp64": (headline["value"] / out["fp64_value"]) if out.get("fp64_value") else None,
         "accuracy": out.get("accuracy"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None,
-                     "peak_source": peak_src, "kernel": "push_mixed (per step)",
+                     "peak_source": peak_src, "kernel": "push_binned_kernel<3>",
+                     "kernel_ms_per_launch": kern_ms,
                      "bytes_per_particle_step": bytes_per},
-        "gpu_launches": out["launches"], "clocks": out["clocks"],
+        "gpu_launches": out["learned"]["gpu_launches"] if "learned" in out else out["launches"],
+        "clocks": out["learned"]["clocks"] if "learned" in out else out["clocks"],
         "k_hist": out["stats"]["k_hist"],
     }
     if "e2e" in out:

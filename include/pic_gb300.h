@@ -66,15 +66,18 @@ extern "C" {
                                warps of equal k                                   */
 #define PIC_SCHED_PREDICTED 2 /* binned, and before each launch the particles an
                                  attached predictor (pic_attach_predictor) expects
-                                 to sub-cycle are binned by predicted k and pushed
-                                 first; the criterion still decides every k      */
+                                 to take a long sub-cycle (k >= 3) are binned by
+                                 predicted k and pushed first (shorter ones are
+                                 left to the stream's in-warp compaction); the
+                                 criterion still decides every k               */
 
 /* per-particle status byte: low 7 bits = k of the last macro step; bit 7 set =
    the particle left the field window and is frozen */
 #define PIC_STATUS_LOST 0x80
 
 typedef struct {
-  double dt;          /* macro step (the field solver's step), > 0               */
+  double dt;          /* macro step (the field solver's step), > 0; the mixed
+                         form also needs 2^-100 <= dt < 2^100 in FP32           */
   double dx;          /* cell size, > 0                                          */
   double psi_max;     /* rotation-angle threshold Psi_max, > 0 (Sec. IV)         */
   double qm;          /* charge/mass in units of |e|/m; -1 for the electron      */
@@ -151,10 +154,11 @@ int pic_stats_read(pic_ctx* ctx, pic_step_stats* stats, int32_t reset);
 /* Replace the stream on which the context queues its work. */
 int pic_set_stream(pic_ctx* ctx, void* stream);
 
-/* Turn CUDA-event timing of the push on (1) or off (0).  When on, every step
- * of pic_push_step is bracketed by two events recorded on the context's
- * stream, around the push kernel launches of that step only.  Errors:
- * PIC_EINVAL, PIC_ECUDA. */
+/* Turn CUDA-event timing of the push on (1) or off (0).  When on, two events
+ * recorded on the context's stream bracket the push kernel launch of every
+ * step of pic_push_step (not the per-step half-step, binning or predictor
+ * kernels; the last step's bracket also holds the call's closing launch).
+ * Errors: PIC_EINVAL, PIC_ECUDA. */
 int pic_timing_enable(pic_ctx* ctx, int32_t on);
 
 /* Sum of the bracketed durations (milliseconds) and the number of timed steps
@@ -218,6 +222,13 @@ int pic_mlp_train_step(pic_mlp* mlp, const float* phi, const uint8_t* label, int
 /* Predicted class (argmax of the logits; ties go to the smaller k) of n
  * samples: pred is device n uint8.  Asynchronous. */
 int pic_mlp_infer(pic_mlp* mlp, const float* phi, int64_t n, uint8_t* pred);
+
+/* pic_features of every loaded particle after macro step n followed by
+ * pic_mlp_infer, fused into one pass (the features never reach memory): the
+ * predictor's class for each particle's next step, in pred (device, one uint8
+ * per loaded particle).  The same classes as the two calls.  Queued on the
+ * context's stream.  Errors: PIC_EINVAL, PIC_ECUDA. */
+int pic_predict(pic_ctx* ctx, const pic_mlp* mlp, int64_t n, uint8_t* pred);
 
 /* ---- batched ensembles (not in the paper) -----------------------------------
  * Many independent problems (each its own dt, dx, Psi_max, q/m, k cap, field-

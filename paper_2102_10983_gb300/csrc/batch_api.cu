@@ -89,7 +89,7 @@ extern "C" int pic_batch_create(const pic_ensemble* ens, int32_t n_ens, int32_t 
     const pic_ensemble& q = ens[e];
     if (!(q.dt > 0) || !(q.dx > 0) || !(q.psi_max > 0) || !isfinite(q.qm) || q.qm == 0.0 ||
         q.k_max < 0 || q.k_max > kMaxK || (q.field_time != 0 && q.field_time != 1) ||
-        q.n_particles < 0)
+        q.n_particles < 0 || !((float)q.dt >= 0x1p-100f && (float)q.dt < 0x1p100f))
       return bfail(nullptr, PIC_EINVAL, "pic_batch_create: an ensemble's parameters are out of range");
     total += q.n_particles;
   }

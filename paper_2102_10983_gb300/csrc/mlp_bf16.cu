@@ -19,6 +19,7 @@
 #include <math.h>
 
 #include "pic_internal.h"
+#include "push_device.cuh"
 
 namespace pic {
 
@@ -195,6 +196,130 @@ __global__ void __launch_bounds__(128) mlp_infer_kernel(const float* P, const fl
       if (base + g + 8 < n) pred[base + g + 8] = (uint8_t)c1;
     }
   }
+}
+
+// ---------------------------------------------------------------- fused features + inference
+
+namespace {
+
+// Inference-only forward of two 16-row tiles that share every weight fragment
+// load; the same MMA sequence per tile as forward_tile, so the same logits.
+__device__ __forceinline__ void infer_tiles2(const SmemW& s, const uint32_t (&x0)[4],
+                                             const uint32_t (&x1)[4], float (&z0)[4],
+                                             float (&z1)[4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  uint32_t h0[4][4], h1[4][4];
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const float bl = s.b1[8 * nt + 2 * t], bh = s.b1[8 * nt + 2 * t + 1];
+    float c0[4] = {bl, bh, bl, bh}, c1[4] = {bl, bh, bl, bh};
+    const __nv_bfloat16* w = s.W1p + (8 * nt + g) * kK1;
+    const uint32_t b0 = ld32(w + 2 * t), b1 = ld32(w + 2 * t + 8);
+    mma16816(c0, x0, b0, b1);
+    mma16816(c1, x1, b0, b1);
+    const int kc = nt >> 1, hi = (nt & 1) * 2;
+    h0[kc][hi] = pack2(fmaxf(c0[0], 0.f), fmaxf(c0[1], 0.f));
+    h0[kc][hi + 1] = pack2(fmaxf(c0[2], 0.f), fmaxf(c0[3], 0.f));
+    h1[kc][hi] = pack2(fmaxf(c1[0], 0.f), fmaxf(c1[1], 0.f));
+    h1[kc][hi + 1] = pack2(fmaxf(c1[2], 0.f), fmaxf(c1[3], 0.f));
+  }
+  uint32_t q0[4][4], q1[4][4];
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const float bl = s.b2[8 * nt + 2 * t], bh = s.b2[8 * nt + 2 * t + 1];
+    float c0[4] = {bl, bh, bl, bh}, c1[4] = {bl, bh, bl, bh};
+    const __nv_bfloat16* w = s.W2 + (8 * nt + g) * kH;
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) {
+      const uint32_t b0 = ld32(w + 16 * kc + 2 * t), b1 = ld32(w + 16 * kc + 2 * t + 8);
+      mma16816(c0, h0[kc], b0, b1);
+      mma16816(c1, h1[kc], b0, b1);
+    }
+    const int kc = nt >> 1, hi = (nt & 1) * 2;
+    q0[kc][hi] = pack2(fmaxf(c0[0], 0.f), fmaxf(c0[1], 0.f));
+    q0[kc][hi + 1] = pack2(fmaxf(c0[2], 0.f), fmaxf(c0[3], 0.f));
+    q1[kc][hi] = pack2(fmaxf(c1[0], 0.f), fmaxf(c1[1], 0.f));
+    q1[kc][hi + 1] = pack2(fmaxf(c1[2], 0.f), fmaxf(c1[3], 0.f));
+  }
+  const float bl = s.b3[2 * t], bh = s.b3[2 * t + 1];
+  z0[0] = bl; z0[1] = bh; z0[2] = bl; z0[3] = bh;
+  z1[0] = bl; z1[1] = bh; z1[2] = bl; z1[3] = bh;
+  const __nv_bfloat16* w = s.W3 + g * kH;
+#pragma unroll
+  for (int kc = 0; kc < 4; ++kc) {
+    const uint32_t b0 = ld32(w + 16 * kc + 2 * t), b1 = ld32(w + 16 * kc + 2 * t + 8);
+    mma16816(z0, q0[kc], b0, b1);
+    mma16816(z1, q1[kc], b0, b1);
+  }
+}
+
+}  // namespace
+
+// Features and prediction in one pass: each warp takes 32 particles (one per
+// lane), forms their features in registers (particle_features, the same code
+// as the features kernel), passes them through a per-warp shared-memory tile
+// into the layer-1 fragments of two 16-row tiles and writes the argmax class.
+// The same predictions as the features kernel followed by mlp_infer_kernel,
+// without the 24 bytes per particle of features going through HBM.
+template <int P>
+__global__ void __launch_bounds__(128) predict_kernel(PushArgsMixed a, const float* Pm,
+                                                      uint8_t* pred) {
+  __shared__ SmemW s;
+  __shared__ float ft[4][32][8];
+  load_weights(s, Pm);
+  __syncthreads();
+  StepFields<P, true> F;
+  load_fields<P, true>(F, a, false);
+  float w[2 * (P + 1)];
+  lagrange_f32<P>(1.5f, w);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  float(&T)[32][8] = ft[warp];
+  T[lane][6] = 0.f;
+  T[lane][7] = 0.f;
+  const int64_t stride = (int64_t)gridDim.x * (blockDim.x >> 5) * 32;
+  for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * 32; base < a.n;
+       base += stride) {
+    float f[6];
+    particle_features<P>(a, F, w, base + lane, f);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) T[lane][q] = f[q];
+    __syncwarp();
+    uint32_t x0[4], x1[4];
+    x0[0] = pack2(T[g][2 * t], T[g][2 * t + 1]);
+    x0[1] = pack2(T[g + 8][2 * t], T[g + 8][2 * t + 1]);
+    x1[0] = pack2(T[g + 16][2 * t], T[g + 16][2 * t + 1]);
+    x1[1] = pack2(T[g + 24][2 * t], T[g + 24][2 * t + 1]);
+    x0[2] = x0[3] = x1[2] = x1[3] = 0u;
+    __syncwarp();
+    float z0[4], z1[4];
+    infer_tiles2(s, x0, x1, z0, z1);
+    int c0, c1, c2, c3;
+    argmax_rows(z0, c0, c1);
+    argmax_rows(z1, c2, c3);
+    if (t == 0) {
+      if (base + g < a.n) pred[base + g] = (uint8_t)c0;
+      if (base + g + 8 < a.n) pred[base + g + 8] = (uint8_t)c1;
+      if (base + g + 16 < a.n) pred[base + g + 16] = (uint8_t)c2;
+      if (base + g + 24 < a.n) pred[base + g + 24] = (uint8_t)c3;
+    }
+  }
+}
+
+cudaError_t launch_predict_fused(const PushArgsMixed& a, int order, const float* P, uint8_t* pred,
+                                 int sm_count, cudaStream_t st) {
+  if (a.n <= 0) return cudaSuccess;
+  const int64_t want = (a.n + 127) / 128;
+  const int64_t cap = (int64_t)(sm_count > 0 ? sm_count : 152) * 8;
+  const int blocks = (int)(want < cap ? want : cap);
+  switch (order) {
+    case 1: predict_kernel<1><<<blocks, 128, 0, st>>>(a, P, pred); break;
+    case 2: predict_kernel<2><<<blocks, 128, 0, st>>>(a, P, pred); break;
+    case 3: predict_kernel<3><<<blocks, 128, 0, st>>>(a, P, pred); break;
+    case 4: predict_kernel<4><<<blocks, 128, 0, st>>>(a, P, pred); break;
+    case 5: predict_kernel<5><<<blocks, 128, 0, st>>>(a, P, pred); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- training (gradients)

@@ -40,8 +40,8 @@ struct pic_ctx {
   int32_t* qcount = nullptr;  // [0,16) deferred counts, 16 cursor, 18 blocks done, [32,40) predicted counts
   // predicted schedule
   uint8_t* pred = nullptr;
-  float* phi = nullptr;
   float* half = nullptr;  // mixed form: E_y, B_z of every window node at the step's t_n
+  float* coef = nullptr;  // mixed form: per node monomial coefficients, two steps (parity of s)
   int32_t* pred_queue = nullptr;
   const pic_mlp* mlp = nullptr;
   int32_t predict_every = 1;
@@ -86,7 +86,8 @@ static void free_all(pic_ctx* c) {
 
   void* ptrs[] = {c->x, c->px, c->py, c->pz, c->cell, c->frac, c->fpx, c->fpy, c->fpz,
                   c->status, c->ringE, c->ringB, c->staging, c->wtab64, c->wtab32,
-                  c->dstats, c->queue, c->qcount, c->pred, c->phi, c->pred_queue, c->half};
+                  c->dstats, c->queue, c->qcount, c->pred, c->pred_queue, c->half,
+                  c->coef};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -182,6 +183,8 @@ extern "C" int pic_create(const pic_params* prm, int64_t capacity, int64_t windo
   if (prm->schedule != PIC_SCHED_PLAIN && prm->schedule != PIC_SCHED_BINNED &&
       prm->schedule != PIC_SCHED_PREDICTED)
     return fail(nullptr, PIC_EINVAL, "pic_create: unknown schedule%s");
+  if (prm->precision == PIC_MIXED && !((float)prm->dt >= 0x1p-100f && (float)prm->dt < 0x1p100f))
+    return fail(nullptr, PIC_EINVAL, "pic_create: the mixed form needs 2^-100 <= dt < 2^100%s");
   if (prm->schedule != PIC_SCHED_PLAIN && prm->precision != PIC_MIXED)
     return fail(nullptr, PIC_EINVAL, "pic_create: the binned schedules need PIC_MIXED%s");
   if (capacity < 0 || capacity > ((int64_t)1 << 31) - 1)
@@ -217,6 +220,7 @@ extern "C" int pic_create(const pic_params* prm, int64_t capacity, int64_t windo
   };
   if (mixed) {
     A((void**)&c->half, 2 * (size_t)window_cells * 4);
+    A((void**)&c->coef, 2 * (size_t)window_cells * 2 * (prm->order + 1) * 4);
     A((void**)&c->cell, cap * 4);
     A((void**)&c->frac, cap * 4);
     A((void**)&c->fpx, cap * 4);
@@ -228,7 +232,6 @@ extern "C" int pic_create(const pic_params* prm, int64_t capacity, int64_t windo
     }
     if (prm->schedule == PIC_SCHED_PREDICTED) {
       A((void**)&c->pred, cap);
-      A((void**)&c->phi, cap * 6 * sizeof(float));
       A((void**)&c->pred_queue, 7 * cap * 4);
     }
   } else {
@@ -561,6 +564,8 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
     base.n = c->n;
     base.cell = c->cell; base.frac = c->frac; base.px = c->fpx; base.py = c->fpy; base.pz = c->fpz;
     base.status = c->status;
+    base.tma = (((uintptr_t)c->cell | (uintptr_t)c->frac | (uintptr_t)c->fpx | (uintptr_t)c->fpy |
+                 (uintptr_t)c->fpz | (uintptr_t)c->status) & 15) == 0;
     base.mask = (int32_t)(W - 1);
     base.dt = (float)c->prm.dt;
     base.psi_max = (float)c->prm.psi_max;
@@ -587,12 +592,13 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
     if (c->n == 0) continue;
     int launches = 0;
     cudaError_t e;
+    // with timing on, two events bracket the push kernel launch(es) of the step
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (c->timing) {
       int rc = timing_pair(c, &ev0, &ev1);
       if (rc != PIC_OK) return rc;
-      CUDA_TRY(c, cudaEventRecord(ev0, c->stream));
     }
+    auto mark = [&](cudaEvent_t ev) { return ev ? cudaEventRecord(ev, c->stream) : cudaSuccess; };
     if (c->prm.precision == PIC_FP64) {
       PushArgsF64 a;
       memset(&a, 0, sizeof(a));
@@ -614,16 +620,24 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
       a.wtab = c->wtab64;
       a.crit_row = wrows_total(c->prm.k_max) - 1;
       a.stats = c->dstats;
-      e = launch_push_f64(a, p, c->stream, &launches);
+      e = mark(ev0);
+      if (e == cudaSuccess) e = launch_push_f64(a, p, c->stream, &launches);
     } else {
       PushArgsMixed a = base;
       fill_mixed(c, a, s, lo, hi, false);
-      // this step's fields at t_n on every window node, for the m = 1 pushes
-      e = launch_halfstep(a, p, W, c->half, c->half + W, c->stream);
+      // this step's fields at t_n on every window node (the m = 1 pushes) and
+      // its node coefficient table (the sub-cycles); the previous step's table
+      // is the other half of c->coef
+      const int64_t coef_stride = W * 2 * (p + 1);
+      float* coef_cur = c->coef + (s & 1) * coef_stride;
+      float* coef_prev = c->coef + ((s - 1) & 1) * coef_stride;
+      e = launch_halfstep(a, p, W, c->half, c->half + W, coef_cur, c->stream);
       ++launches;
       if (e != cudaSuccess) return fail(c, PIC_ECUDA, "half-step launch: %s", cudaGetErrorString(e));
       a.halfE = c->half;
       a.halfB = c->half + W;
+      a.coef = coef_cur;
+      a.coef_p = j > 0 ? coef_prev : coef_cur;
       if (binned) {
         const int64_t qsz = 7 * c->capacity;
         if (j > 0) {
@@ -649,19 +663,19 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
           if (j % c->predict_every == 0 && step_slots(c, s - 1, ps, &plo, &phi) == PIC_OK) {
             PushArgsMixed fa = a;
             fill_mixed(c, fa, s - 1, plo, phi, false);
-            e = launch_features_mixed(fa, p, c->phi, c->stream);
-            if (e == cudaSuccess)
-              e = launch_mlp_infer(mlp_device_params(c->mlp), c->phi, c->n, c->pred, c->sm_count,
-                                   c->stream);
-            launches += 2;
+            fa.coef = fa.coef_p = nullptr;
+            e = launch_predict_fused(fa, p, mlp_device_params(c->mlp), c->pred, c->sm_count,
+                                     c->stream);
+            ++launches;
           }
           if (e == cudaSuccess)
-            e = launch_bin_predicted(c->pred, c->status, c->n, a.parity_cur, c->pred_queue,
+            e = launch_bin_predicted(c->pred, c->status, c->n, a.parity_cur, kDeferMin, c->pred_queue,
                                      c->qcount + 32, c->capacity, c->stream);
           ++launches;
           a.pred_queue = c->pred_queue;
           a.pred_count = c->qcount + 32;
         }
+        if (e == cudaSuccess) e = mark(ev0);
         if (e == cudaSuccess)
           e = launch_binned_step(a, p, c->sm_count, c->stream, &launches);
         if (e == cudaSuccess && j == n_steps - 1) {
@@ -673,12 +687,15 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
           f.queue_out = c->queue + ((n_steps + 1) & 1) * qsz;
           f.qcount_out = c->qcount + ((n_steps + 1) & 1) * 8;
           f.finalize = 1;
+          f.coef_p = coef_cur;  // the deferred work finishes this (the last) step
           f.pred_queue = nullptr;
           f.pred_count = nullptr;
           e = launch_binned_step(f, p, c->sm_count, c->stream, &launches);
         }
       } else {
-        e = launch_push_mixed(a, p, c->prm.schedule, c->sm_count, c->stream, &launches);
+        e = mark(ev0);
+        if (e == cudaSuccess)
+          e = launch_push_mixed(a, p, c->prm.schedule, c->sm_count, c->stream, &launches);
       }
     }
     c->launches += launches;
@@ -704,6 +721,26 @@ extern "C" int pic_features(pic_ctx* c, int64_t n, float* phi) {
   a.mask = (int32_t)(c->W - 1);
   fill_mixed(c, a, n, lo, hi, false);
   CUDA_TRY(c, launch_features_mixed(a, c->prm.order, phi, c->stream));
+  ++c->launches;
+  return PIC_OK;
+}
+
+extern "C" int pic_predict(pic_ctx* c, const pic_mlp* mlp, int64_t n, uint8_t* pred) {
+  if (!c || !mlp || (!pred && c->n > 0)) return PIC_EINVAL;
+  if (c->prm.precision != PIC_MIXED) return fail(c, PIC_EINVAL, "pic_predict: needs the mixed form%s");
+  int slots[kMaxOrder + 1];
+  int64_t lo, hi;
+  int rc = step_slots(c, n, slots, &lo, &hi);
+  if (rc != PIC_OK) return rc;
+  PushArgsMixed a;
+  memset(&a, 0, sizeof(a));
+  a.n = c->n;
+  a.cell = c->cell; a.frac = c->frac; a.px = c->fpx; a.py = c->fpy; a.pz = c->fpz;
+  a.status = c->status;
+  a.mask = (int32_t)(c->W - 1);
+  fill_mixed(c, a, n, lo, hi, false);
+  CUDA_TRY(c, launch_predict_fused(a, c->prm.order, mlp_device_params(mlp), pred, c->sm_count,
+                                   c->stream));
   ++c->launches;
   return PIC_OK;
 }

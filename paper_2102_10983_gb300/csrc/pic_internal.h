@@ -11,6 +11,10 @@ namespace pic {
 
 constexpr int kMaxOrder = 5;
 constexpr int kMaxK = 7;
+// Binned schedule: smallest k whose sub-cycle is deferred to the next launch's
+// first work items (shorter ones are compacted inside the warp); also the
+// smallest predicted k the predicted schedule bins before a launch.
+constexpr int kDeferMin = 3;
 
 // Device counters of one context (accumulated by every push launch).
 struct DevStats {
@@ -75,6 +79,11 @@ struct PushArgsMixed {
   // by the step's half-step kernel; nullptr = not provided (gather the levels)
   const float* halfE;
   const float* halfB;
+  // per window node, the monomial coefficients of the temporal interpolant of
+  // E_y (p+1) then B_z (p+1) for this step (coef) and the previous one
+  // (coef_p); nullptr = form them from the levels
+  const float* coef;
+  const float* coef_p;
   int32_t lo, hi;      // tent node j must satisfy lo <= j and j+1 <= hi
   int32_t lo_p, hi_p;  // same for the previous step
   int32_t mask;
@@ -98,6 +107,7 @@ struct PushArgsMixed {
   unsigned* blocks_done;  // blocks finished
   int parity_cur, parity_next;
   int finalize;
+  int tma;  // 1: the six particle arrays are 16-byte aligned (stream tiles by bulk copy)
   // predicted schedule: electrons binned before the launch by predicted k
   // (per-k queues, qcap entries each), pushed by this launch in full
   const int32_t* pred_queue;
@@ -174,13 +184,16 @@ cudaError_t launch_push_mixed(const PushArgsMixed& a, int order, int schedule, i
 // call (the last step's deferred particles, then public status bytes).
 cudaError_t launch_binned_step(const PushArgsMixed& a, int order, int sm_count, cudaStream_t main,
                                int* launches);
-// E_y, B_z of every window node at t_n (the theta = 1/2 weights of a's step).
+// E_y, B_z of every window node at t_n (the theta = 1/2 weights of a's step),
+// and (coef != nullptr) every node's monomial coefficients, 2(p+1) floats.
 cudaError_t launch_halfstep(const PushArgsMixed& a, int order, int64_t W, float* outE, float* outB,
-                            cudaStream_t s);
+                            float* coef, cudaStream_t s);
 cudaError_t launch_features_mixed(const PushArgsMixed& a, int order, float* phi, cudaStream_t s);
 
+// Bins the particles whose predicted k is >= min_k (and that the stream would
+// take this step) into per-k queues.
 cudaError_t launch_bin_predicted(const uint8_t* pred, uint8_t* status, int64_t n, int parity_cur,
-                                 int32_t* pred_queue, int32_t* pred_count, int64_t qcap,
+                                 int min_k, int32_t* pred_queue, int32_t* pred_count, int64_t qcap,
                                  cudaStream_t s);
 
 // predictor (mlp_bf16.cu, mlp_api.cu)
@@ -188,6 +201,10 @@ const float* mlp_device_params(const struct ::pic_mlp* m);
 int mlp_param_count();
 cudaError_t launch_mlp_infer(const float* P, const float* phi, int64_t n, uint8_t* pred,
                              int sm_count, cudaStream_t s);
+// Features of step a's levels (theta = 3/2) and the predicted class of every
+// particle in one pass (same predictions as features + launch_mlp_infer).
+cudaError_t launch_predict_fused(const PushArgsMixed& a, int order, const float* P, uint8_t* pred,
+                                 int sm_count, cudaStream_t s);
 cudaError_t launch_mlp_grad(const float* P, const float* phi, const uint8_t* label, int64_t n,
                             float* grad, float* loss, int sm_count, cudaStream_t s);
 cudaError_t launch_mlp_adam(float* P, const float* grad, float* m1, float* m2, float lr, int step,

@@ -35,6 +35,7 @@ __device__ __forceinline__ void ens_fields(const BatchArgs& a, const EnsDev& e, 
     lo = o > lo ? o : lo;
     hi = o + a.lstride - 1 < hi ? o + a.lstride - 1 : hi;
   }
+  F.coef = nullptr;  // coefficients formed from the levels
   F.lo = (int32_t)lo;
   F.hi = (int32_t)hi;
 }
@@ -47,6 +48,7 @@ __device__ __forceinline__ int64_t queue_slot(const BatchArgs& a, const EnsDev& 
 // Warp-aggregated enqueue into ensemble ens's queue of k (key = ens * 8 + k;
 // key < 0: nothing).  All 32 lanes call this.
 __device__ __forceinline__ void batch_enqueue(const BatchArgs& a, int key, int32_t i) {
+  if (!__any_sync(0xffffffffu, key >= 0)) return;
   const unsigned peers = __match_any_sync(0xffffffffu, key);
   const int lane = threadIdx.x & 31;
   const int leader = __ffs(peers) - 1;
@@ -321,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, 2) push_batch_kernel(BatchArgs a) {
           count_step(tc, sh, k, capped);
           const int k_prev = st & 7;
           if (k == 0) {
-            const float h_old = ldexpf(e.dt, -2 * k_prev);
+            const float h_old = pow4_down(e.dt, k_prev);
             const float hp = __fmul_rn(0.5f, __fadd_rn(h_old, e.dt));
             boris_f32(ey, b0, hp, hx0, e.qm, s);
             normalize(s);

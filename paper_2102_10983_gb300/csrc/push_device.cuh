@@ -1,6 +1,6 @@
 // Per-particle device arithmetic of the mixed-precision push, shared by the
-// single-problem kernels (push_mixed.cu) and the batched kernel (push_batch.cu).
-// Included in namespace pic by those translation units only.
+// single-problem kernels (push_mixed.cu), the batched kernel (push_batch.cu)
+// and the fused predictor kernel (mlp_bf16.cu).
 #pragma once
 
 #include <limits.h>
@@ -68,18 +68,29 @@ __device__ __forceinline__ float norm2(float a, float b, float c) {
 }
 
 // Criterion (Sec. IV) in FP32: Psi0 = |q/m| |B| dt / (2 gamma); smallest k with
-// Psi0 / 4^k <= Psi_max, capped at k_max.
+// Psi0 / 4^k <= Psi_max, capped at k_max.  Taken in squared form, with no
+// square root and no division: Psi0 <= Psi_max 4^k  <=>
+// (|q/m| dt B)^2 <= (2 Psi_max)^2 (1 + |p|^2) 16^k, and the right side is
+// scaled by 16 (exactly) per step of k.
 __device__ __forceinline__ int psi_to_k(float b0, const MixedState& s, float qm_abs, float dt,
                                         float psi_max, int k_max, bool& capped) {
-  const float g0 = __fsqrt_rn(__fadd_rn(1.0f, norm2(s.ux, s.uy, s.uz)));
-  float psi = __fdiv_rn(__fmul_rn(__fmul_rn(qm_abs, fabsf(b0)), dt), __fmul_rn(2.0f, g0));
+  const float a = __fmul_rn(__fmul_rn(qm_abs, dt), b0);
+  const float a2 = __fmul_rn(a, a);
+  const float tp = __fmul_rn(2.0f, psi_max);
+  float rhs = __fmul_rn(__fmul_rn(tp, tp), __fadd_rn(1.0f, norm2(s.ux, s.uy, s.uz)));
   int k = 0;
-  while (psi > psi_max && k < k_max) {
-    psi = __fmul_rn(psi, 0.25f);
+  while (a2 > rhs && k < k_max) {
+    rhs = __fmul_rn(rhs, 16.0f);
     ++k;
   }
-  capped = psi > psi_max;
+  capped = a2 > rhs;
   return k;
+}
+
+// dt / 4^k for a normal dt whose quotient stays normal (checked by the host):
+// the exponent field lowered by 2k, the same bits as ldexpf(dt, -2k).
+__device__ __forceinline__ float pow4_down(float dt, int k) {
+  return __int_as_float(__float_as_int(dt) - (k << 24));
 }
 
 // b0 is B_z at the particle and t_n: with m = 1 it is also the first (and only)
@@ -93,31 +104,57 @@ __device__ __forceinline__ int criterion_f32(const LV& B, const float* wcrit, in
   return psi_to_k(b0, s, qm_abs, dt, psi_max, k_max, capped);
 }
 
-// Field view of one macro step.
+// Field view of one macro step.  coef (optional): per window node, the
+// monomial coefficients (to_monomial) of the temporal interpolant of E_y (P+1)
+// then of B_z (P+1), written once per step by the half-step kernel, so a node
+// change costs two contiguous loads per grid instead of 2(P+1) scattered ones.
 template <int P, bool RING>
 struct StepFields {
   Levels<P, RING> E, B;
+  const float* coef;
   int32_t lo, hi;
 };
 
+// Single-instruction reciprocal and reciprocal square root (the SFU's
+// approximations, ~2 ulp, subnormals flushed): every schedule of the mixed form
+// calls these same two, so they agree bit for bit.  Their arguments here are
+// 1 + |p|^2 >= 1 and 1 + t^2 >= 1.
+__device__ __forceinline__ float rsqrt_sfu(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_sfu(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // One Boris sub-step (Eqs. eq:p - eq:gamman) and the position update (Eq. eq:x)
 // in the fields ey, bz, with momentum step hp and offset step hx (cells per
-// unit velocity).
+// unit velocity).  The operations are ordered for the serial chain of a long
+// sub-cycle: the terms of 1 + |p|^2 known early are summed first, so the
+// component that arrives last costs a single FMA before each square root.
 __device__ __forceinline__ void boris_f32(float ey, float bz, float hp, float hx, float qm,
                                           MixedState& s) {
-  const float half = __fmul_rn(0.5f, hp);
-  const float dpy = __fmul_rn(__fmul_rn(qm, ey), half);
-  const float mx = s.ux, my = __fadd_rn(s.uy, dpy), mz = s.uz;
-  const float inv_gn = rsqrtf(__fadd_rn(1.0f, norm2(mx, my, mz)));
-  const float tz = __fmul_rn(__fmul_rn(__fmul_rn(qm, bz), half), inv_gn);
+  const float qmh = __fmul_rn(qm, __fmul_rn(0.5f, hp));  // q/m hp/2
+  const float dpy = __fmul_rn(qmh, ey);
+  const float mx = s.ux, mz = s.uz;
+  const float g2xz = __fadd_rn(1.0f, __fmaf_rn(mz, mz, __fmul_rn(mx, mx)));
+  const float my = __fadd_rn(s.uy, dpy);
+  const float inv_gn = rsqrt_sfu(__fmaf_rn(my, my, g2xz));
+  const float tz = __fmul_rn(__fmul_rn(qmh, bz), inv_gn);
   const float ppx = __fmaf_rn(my, tz, mx);
   const float ppy = __fmaf_rn(-mx, tz, my);
-  const float sz = __fdividef(__fmul_rn(2.0f, tz), __fmaf_rn(tz, tz, 1.0f));
-  s.ux = __fmaf_rn(ppy, sz, mx);
-  s.uy = __fadd_rn(__fmaf_rn(-ppx, sz, my), dpy);
+  const float sz = __fmul_rn(__fmul_rn(2.0f, tz), rcp_sfu(__fmaf_rn(tz, tz, 1.0f)));
+  const float ux = __fmaf_rn(ppy, sz, mx);
+  const float uy = __fadd_rn(__fmaf_rn(-ppx, sz, my), dpy);
+  s.ux = ux;
+  s.uy = uy;
   s.uz = mz;
-  const float inv_g = rsqrtf(__fadd_rn(1.0f, norm2(s.ux, s.uy, s.uz)));
-  s.frac = __fmaf_rn(hx, __fmul_rn(s.ux, inv_g), s.frac);
+  const float g2n = __fadd_rn(1.0f, __fmaf_rn(mz, mz, __fmul_rn(ux, ux)));
+  const float inv_g = rsqrt_sfu(__fmaf_rn(uy, uy, g2n));
+  s.frac = __fmaf_rn(hx, __fmul_rn(ux, inv_g), s.frac);
 }
 
 // Reciprocal of prod_{k != j} (j - k), the denominator of L_{p,j} (Sec. VI).
@@ -186,6 +223,21 @@ __device__ __forceinline__ void to_monomial(const LV& lv, int32_t a0, int32_t a1
   }
 }
 
+// Coefficients of nodes a0, a1 of one grid (g = 0: E, 1: B) from the step's
+// table; the same values to_monomial computes from the levels.
+template <int P>
+__device__ __forceinline__ void table_coefs(const float* coef, int g, int32_t a0, int32_t a1,
+                                            float* c0, float* c1) {
+  constexpr int S = 2 * (P + 1);
+  const float* r0 = coef + (int64_t)a0 * S + g * (P + 1);
+  const float* r1 = coef + (int64_t)a1 * S + g * (P + 1);
+#pragma unroll
+  for (int q = 0; q <= P; ++q) {
+    c0[q] = __ldg(r0 + q);
+    c1[q] = __ldg(r1 + q);
+  }
+}
+
 template <int P>
 __device__ __forceinline__ float horner(const float* c, float u) {
   float f = c[P];
@@ -200,15 +252,21 @@ __device__ __forceinline__ float horner(const float* c, float u) {
 // u = theta - 1; its coefficients are formed when the node index changes (an
 // electron moves a small fraction of a cell per sub-step) and each sub-step
 // evaluates it by Horner's rule: p FMAs per node, nothing waits on memory.
-template <int P, bool RING>
+// The floors of the offset on both grids are cached with the coefficients, so
+// while the nodes stay the same a sub-step's tent weights are one subtraction
+// each after the new offset (the same bits as a fresh floor).  The
+// coefficients come from
+// the step's node table (TABLE: F.coef, written by the half-step kernel), else
+// from the levels.
+template <int P, bool RING, bool TABLE = false>
 __device__ __forceinline__ bool subcycle_f32(const StepFields<P, RING>& F, const float* wtab,
                                              int32_t mask, float dt, float inv_dx, float qm,
                                              int field_time,
                                              const float (&mono)[2][kMaxOrder + 1][kMaxOrder + 1],
                                              int k, int k_prev, float b0, MixedState& s) {
   constexpr int stride = 2 * (P + 1);
-  const float h = ldexpf(dt, -2 * k);
-  const float h_old = ldexpf(dt, -2 * k_prev);
+  const float h = pow4_down(dt, k);
+  const float h_old = pow4_down(dt, k_prev);
   const float hx = __fmul_rn(h, inv_dx);
   float hp = __fmul_rn(0.5f, __fadd_rn(h_old, h));
   if (k == 0) {
@@ -221,29 +279,45 @@ __device__ __forceinline__ bool subcycle_f32(const StepFields<P, RING>& F, const
     return true;
   }
   const int m = 1 << (2 * k);
-  const float inv_m = ldexpf(1.0f, -2 * k);
+  const float inv_m = pow4_down(1.0f, k);
   // u_j = theta_j - 1, exact in FP32 for m <= 4^7
   const float u1 = field_time == 0 ? -0.5f : __fsub_rn(__fmul_rn(0.5f, inv_m), 1.0f);
   int32_t ce = INT_MIN, cb = INT_MIN;
   float ce0[P + 1], ce1[P + 1], cb0[P + 1], cb1[P + 1];  // monomial coefficients per node
+#pragma unroll
+  for (int q = 0; q <= P; ++q) ce0[q] = ce1[q] = cb0[q] = cb1[q] = 0.f;
+  // floors of the offset on the two grids at the cached nodes (NaN: none yet)
+  float fe = __int_as_float(0x7fc00000), fb = fe;
   for (int j = 1; j <= m; ++j) {
     const float u = __fmaf_rn((float)(j - 1), inv_m, u1);
-    int32_t je, jb;
-    float we, wb;
-    if (!tent_coords(s.cell, s.frac, F.lo, F.hi, je, we, jb, wb)) return false;
-    if (je != ce) {
-      ce = je;
-      to_monomial<P>(F.E, je & mask, (je + 1) & mask, mono[0], ce0, ce1);
+    const float f = s.frac;
+    const float fbm = __fsub_rn(f, 0.5f);
+    if (!(f >= fe && f < __fadd_rn(fe, 1.0f) && fbm >= fb && fbm < __fadd_rn(fb, 1.0f))) {
+      int32_t je, jb;
+      float we, wb;
+      if (!tent_coords(s.cell, f, F.lo, F.hi, je, we, jb, wb)) return false;
+      fe = floorf(f);
+      fb = floorf(fbm);
+      if (je != ce) {
+        ce = je;
+        if constexpr (TABLE)
+          table_coefs<P>(F.coef, 0, je & mask, (je + 1) & mask, ce0, ce1);
+        else
+          to_monomial<P>(F.E, je & mask, (je + 1) & mask, mono[0], ce0, ce1);
+      }
+      if (jb != cb) {
+        cb = jb;
+        if constexpr (TABLE)
+          table_coefs<P>(F.coef, 1, jb & mask, (jb + 1) & mask, cb0, cb1);
+        else
+          to_monomial<P>(F.B, jb & mask, (jb + 1) & mask, mono[1], cb0, cb1);
+      }
     }
-    if (jb != cb) {
-      cb = jb;
-      to_monomial<P>(F.B, jb & mask, (jb + 1) & mask, mono[1], cb0, cb1);
-    }
+    const float we = __fsub_rn(f, fe), wb = __fsub_rn(fbm, fb);
     const float fe0 = horner<P>(ce0, u), fe1 = horner<P>(ce1, u);
     const float fb0 = horner<P>(cb0, u), fb1 = horner<P>(cb1, u);
-    const float ey = __fmaf_rn(we, __fsub_rn(fe1, fe0), fe0);
-    const float bz = __fmaf_rn(wb, __fsub_rn(fb1, fb0), fb0);
-    boris_f32(ey, bz, hp, hx, qm, s);
+    boris_f32(__fmaf_rn(we, __fsub_rn(fe1, fe0), fe0), __fmaf_rn(wb, __fsub_rn(fb1, fb0), fb0), hp,
+              hx, qm, s);
     hp = h;
   }
   return true;
@@ -257,10 +331,13 @@ __device__ __forceinline__ void normalize(MixedState& s) {
 
 // ---------------------------------------------------------------- counters
 
-// Per-thread counters: k = 0 steps and sub-step sums in registers; rare events
-// (k > 0, caps, losses) straight into shared memory.
+// Per-thread counters in registers: steps with k = 0, 1, 2 (the common ones),
+// caps, sub-step sums.  Steps with k >= 3 are rare and go straight into the
+// block's shared counters.  (Shared-memory atomics on one address for every
+// sub-cycled particle serialised the warps at a front.)
 struct ThreadCounters {
-  unsigned long long k0 = 0, sub = 0, star = 0;
+  unsigned k0 = 0, k1 = 0, k2 = 0, capped = 0;
+  unsigned long long sub = 0, star = 0;
 };
 
 __device__ __forceinline__ void count_step(ThreadCounters& tc, unsigned long long* sh, int k,
@@ -271,9 +348,14 @@ __device__ __forceinline__ void count_step(ThreadCounters& tc, unsigned long lon
     ++tc.k0;
   } else {
     tc.star += m;
-    atomicAdd(&sh[k], 1ull);
+    if (k == 1)
+      ++tc.k1;
+    else if (k == 2)
+      ++tc.k2;
+    else
+      atomicAdd(&sh[k], 1ull);
   }
-  if (capped) atomicAdd(&sh[10], 1ull);
+  tc.capped += capped ? 1u : 0u;
 }
 
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
@@ -285,11 +367,16 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 // All threads of the block must call this.
 __device__ __forceinline__ void flush_counters(const ThreadCounters& tc, unsigned long long* sh,
                                                DevStats* st) {
-  const unsigned long long k0 = warp_sum(tc.k0), sub = warp_sum(tc.sub), star = warp_sum(tc.star);
+  const unsigned long long k0 = warp_sum(tc.k0), k1 = warp_sum(tc.k1), k2 = warp_sum(tc.k2);
+  const unsigned long long cap = warp_sum(tc.capped);
+  const unsigned long long sub = warp_sum(tc.sub), star = warp_sum(tc.star);
   if ((threadIdx.x & 31) == 0) {
     if (k0) atomicAdd(&sh[0], k0);
+    if (k1) atomicAdd(&sh[1], k1);
+    if (k2) atomicAdd(&sh[2], k2);
     if (sub) atomicAdd(&sh[8], sub);
     if (star) atomicAdd(&sh[9], star);
+    if (cap) atomicAdd(&sh[10], cap);
   }
   __syncthreads();
   if (threadIdx.x < 12) {
@@ -323,6 +410,109 @@ __device__ __forceinline__ void store_state(const PushArgsMixed& a, int64_t i, c
   a.pz[i] = s.uz;
 }
 
+// The stream's loads and stores: each state word is touched once per step and
+// the whole state is larger than L2, so these are marked evict-first to leave
+// L2 to the field levels, half-step fields and queues.
+__device__ __forceinline__ void fetch_stream(const PushArgsMixed& a, int64_t i, uint8_t& st,
+                                             MixedState& s) {
+  st = PIC_STATUS_LOST;
+  s = {0, 0.5f, 0.f, 0.f, 0.f};
+  if (i < a.n) {
+    st = __ldcs(a.status + i);
+    s.cell = __ldcs(a.cell + i);
+    s.frac = __ldcs(a.frac + i);
+    s.ux = __ldcs(a.px + i);
+    s.uy = __ldcs(a.py + i);
+    s.uz = __ldcs(a.pz + i);
+  }
+}
+
+__device__ __forceinline__ void store_stream(const PushArgsMixed& a, int64_t i, const MixedState& s) {
+  __stcs(a.cell + i, s.cell);
+  __stcs(a.frac + i, s.frac);
+  __stcs(a.px + i, s.ux);
+  __stcs(a.py + i, s.uy);
+  __stcs(a.pz + i, s.uz);
+}
+
+// ---------------------------------------------------------------- bulk-copy staging of particle tiles
+
+// A tile of kTile consecutive particles' state as the stream reads it from
+// shared memory; filled by six bulk copies (cp.async.bulk, the TMA engine's
+// linear mode) that complete on one mbarrier.  Every member starts on a
+// 128-byte boundary and the size is a multiple of 16 bytes.
+#ifndef PIC_TILE
+#define PIC_TILE 128
+#endif
+constexpr int kTile = PIC_TILE;
+struct Tile {
+  int32_t cell[kTile];
+  float frac[kTile], px[kTile], py[kTile], pz[kTile];
+  uint8_t st[kTile];
+};
+constexpr uint32_t kTileBytes = (uint32_t)sizeof(Tile);
+static_assert(sizeof(Tile) % 16 == 0, "bulk copies move multiples of 16 bytes");
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+// Make the initialised barriers visible to the bulk-copy (async) proxy.
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for phase `parity` of the barrier to complete, giving up after a bound
+// (each try_wait itself blocks for a while): false = the copies never landed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 24); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// L2 policy for the particle stream: each word is used once per step and the
+// whole state is larger than L2.
+__device__ __forceinline__ uint64_t evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void bulk_to_smem(void* dst, const void* src, uint32_t bytes,
+                                             uint64_t* bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1], %2, [%3], %4;" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+      : "memory");
+}
+// One lane: stage particles [first, first + kTile) into t (all of them exist,
+// the arrays are 16-byte aligned and first is a multiple of kTile).
+__device__ __forceinline__ void tile_issue(const PushArgsMixed& a, Tile* t, uint64_t* bar,
+                                           int64_t first, uint64_t policy) {
+  mbar_expect(bar, kTileBytes);
+  bulk_to_smem(t->cell, a.cell + first, kTile * 4, bar, policy);
+  bulk_to_smem(t->frac, a.frac + first, kTile * 4, bar, policy);
+  bulk_to_smem(t->px, a.px + first, kTile * 4, bar, policy);
+  bulk_to_smem(t->py, a.py + first, kTile * 4, bar, policy);
+  bulk_to_smem(t->pz, a.pz + first, kTile * 4, bar, policy);
+  bulk_to_smem(t->st, a.status + first, kTile, bar, policy);
+}
+
 // The current (prev = false) or previous step's field view from the launch
 // arguments: ring form from the mirrored ring's start slot, pointer form from
 // the per-level pointers.
@@ -342,16 +532,54 @@ __device__ __forceinline__ void load_fields(StepFields<P, RING>& F, const PushAr
       F.B.ptr[l] = prev ? a.Bp[l] : a.B[l];
     }
   }
+  F.coef = prev ? a.coef_p : a.coef;
   F.lo = prev ? a.lo_p : a.lo;
   F.hi = prev ? a.hi_p : a.hi;
+}
+
+// ---------------------------------------------------------------- predictor features
+
+// phi = (asinh|E|, asinh|B|, asinh p_x, asinh p_y, asinh p_z, log gamma) of
+// particle i after macro step n, with E and B at its position extrapolated to
+// t_{n+1} (theta = 3/2, weights w) from step n's levels F: everything known
+// before level n+1 arrives.  Lost particles and i >= n get zeros; E and B are
+// zero outside the window.
+template <int P>
+__device__ __forceinline__ void particle_features(const PushArgsMixed& a, const StepFields<P, true>& F,
+                                                  const float* w, int64_t i, float (&f)[6]) {
+#pragma unroll
+  for (int q = 0; q < 6; ++q) f[q] = 0.f;
+  if (i >= a.n) return;
+  const uint8_t st = a.status[i];
+  if (st & PIC_STATUS_LOST) return;
+  const MixedState s = load_state(a, i);
+  int32_t je, jb;
+  float we, wb;
+  if (tent_coords(s.cell, s.frac, F.lo, F.hi, je, we, jb, wb)) {
+    const float ey = gather_f32<P>(F.E, w, je, we, a.mask);
+    const float bz = gather_f32<P>(F.B, w + (P + 1), jb, wb, a.mask);
+    f[0] = asinhf(fabsf(ey));
+    f[1] = asinhf(fabsf(bz));
+  }
+  f[2] = asinhf(s.ux);
+  f[3] = asinhf(s.uy);
+  f[4] = asinhf(s.uz);
+  f[5] = 0.5f * log1pf(norm2(s.ux, s.uy, s.uz));
 }
 
 // ---------------------------------------------------------------- binned schedule pieces
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kChunk = 256;          // particles per stream item (8 per lane)
-constexpr int kDeferMin = 3;         // smallest k that is deferred
+#ifndef PIC_CHUNK
+#define PIC_CHUNK 512
+#endif
+#ifndef PIC_STAGES
+#define PIC_STAGES 2
+#endif
+constexpr int kChunk = PIC_CHUNK;    // particles per stream item (kChunk / kTile tiles)
+constexpr int kStages = PIC_STAGES;  // staged tiles per warp (one in flight while one is pushed)
+static_assert(kChunk % kTile == 0 && kTile % 32 == 0, "a stream item is whole tiles of whole warps");
 constexpr int kStashK = kDeferMin - 1;
 constexpr int kStashCap = 64;
 constexpr uint8_t kParity = 0x08;
@@ -362,6 +590,7 @@ __device__ __forceinline__ int deferred_k(uint8_t st) { return (st >> 4) & 7; }
 // Enqueue particle i into the queue of its k; warp-aggregated: one atomic per
 // distinct k in the warp.  All 32 lanes call this; key 0 = nothing.
 __device__ __forceinline__ void enqueue(const PushArgsMixed& a, int key, int32_t i) {
+  if (!__any_sync(0xffffffffu, key != 0)) return;
   const unsigned peers = __match_any_sync(0xffffffffu, key);
   const int lane = threadIdx.x & 31;
   const int leader = __ffs(peers) - 1;
@@ -392,8 +621,8 @@ __device__ __forceinline__ void stash_drain(const PushArgsMixed& a, const StepFi
   if (lane < cnt) {
     MixedState s = {S.cell[lane], S.frac[lane], S.ux[lane], S.uy[lane], S.uz[lane]};
     const int32_t i = S.idx[lane];
-    const bool ok = subcycle_f32<P>(F, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, a.field_time, a.mono,
-                                    k, S.kp[lane], 0.f, s);
+    const bool ok = subcycle_f32<P, RING, RING>(F, a.wtab, a.mask, a.dt, a.inv_dx, a.qm,
+                                                a.field_time, a.mono, k, S.kp[lane], 0.f, s);
     normalize(s);
     store_state(a, i, s);
     a.status[i] = ok ? (uint8_t)(k | (a.parity_next ? kParity : 0)) : (uint8_t)(k | PIC_STATUS_LOST);
@@ -428,8 +657,8 @@ __device__ __forceinline__ void heavy_particle(const PushArgsMixed& a, const Ste
   const int k = deferred_k(st);
   const int k_prev = st & 7;
   MixedState s = load_state(a, i);
-  const bool ok = subcycle_f32<P>(Fp, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, a.field_time, a.mono,
-                                  k, k_prev, 0.f, s);
+  const bool ok = subcycle_f32<P, RING, RING>(Fp, a.wtab, a.mask, a.dt, a.inv_dx, a.qm,
+                                              a.field_time, a.mono, k, k_prev, 0.f, s);
   normalize(s);
   if (!ok) {
     store_state(a, i, s);
@@ -456,8 +685,8 @@ __device__ __forceinline__ void heavy_particle(const PushArgsMixed& a, const Ste
                                   a.k_max, capped, b0);
   count_step(tc, sh, kn, capped);
   if (kn < kDeferMin) {
-    const bool ok2 = subcycle_f32<P>(Fc, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, a.field_time,
-                                     a.mono, kn, k, b0, s);
+    const bool ok2 = subcycle_f32<P, RING, RING>(Fc, a.wtab, a.mask, a.dt, a.inv_dx, a.qm,
+                                                 a.field_time, a.mono, kn, k, b0, s);
     normalize(s);
     store_state(a, i, s);
     a.status[i] = ok2 ? (uint8_t)(kn | (a.parity_next ? kParity : 0)) : (uint8_t)(kn | PIC_STATUS_LOST);
@@ -469,15 +698,19 @@ __device__ __forceinline__ void heavy_particle(const PushArgsMixed& a, const Ste
   }
 }
 
-// Predicted item: particle i was binned before the launch as likely to
-// sub-cycle; take its exact criterion and all its sub-steps now.
+// Predicted item: particle i was binned before the launch as likely to take
+// k_pred; take its exact criterion.  k = 0 or k = k_pred: pushed at once.
+// Otherwise it goes where the stream would send it: k < kDeferMin to the
+// caller's stash (sk, with its state s and k_prev kp), else deferred (key).
 template <int P, bool RING>
 __device__ __forceinline__ void predicted_particle(const PushArgsMixed& a, const StepFields<P, RING>& Fc,
-                                                   const float* wcrit, int64_t i, ThreadCounters& tc,
-                                                   unsigned long long* sh) {
+                                                   const float* wcrit, int64_t i, int k_pred,
+                                                   ThreadCounters& tc, unsigned long long* sh,
+                                                   int& key, int& sk, MixedState& s, uint8_t& kp) {
   const uint8_t st = a.status[i];
   const int k_prev = st & 7;
-  MixedState s = load_state(a, i);
+  kp = (uint8_t)k_prev;
+  s = load_state(a, i);
   int32_t je, jb;
   float we, wb;
   if (!tent_coords(s.cell, s.frac, Fc.lo, Fc.hi, je, we, jb, wb)) {
@@ -490,12 +723,19 @@ __device__ __forceinline__ void predicted_particle(const PushArgsMixed& a, const
   const int k = criterion_f32<P>(Fc.B, wcrit, jb, wb, a.mask, s, a.qm_abs, a.dt, a.psi_max,
                                  a.k_max, capped, b0);
   count_step(tc, sh, k, capped);
-  const bool ok = subcycle_f32<P>(Fc, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, a.field_time, a.mono,
-                                  k, k_prev, b0, s);
-  normalize(s);
-  store_state(a, i, s);
-  a.status[i] = ok ? (uint8_t)(k | (a.parity_next ? kParity : 0)) : (uint8_t)(k | PIC_STATUS_LOST);
-  if (!ok) atomicAdd(&sh[11], 1ull);
+  if (k == 0 || k == k_pred) {
+    const bool ok = subcycle_f32<P, RING, RING>(Fc, a.wtab, a.mask, a.dt, a.inv_dx, a.qm,
+                                                a.field_time, a.mono, k, k_prev, b0, s);
+    normalize(s);
+    store_state(a, i, s);
+    a.status[i] = ok ? (uint8_t)(k | (a.parity_next ? kParity : 0)) : (uint8_t)(k | PIC_STATUS_LOST);
+    if (!ok) atomicAdd(&sh[11], 1ull);
+  } else if (k < kDeferMin) {
+    sk = k;
+  } else {
+    a.status[i] = (uint8_t)(k_prev | (k << 4));
+    key = k;
+  }
 }
 
 }  // namespace pic

@@ -19,7 +19,8 @@
 // Schedules:
 //  PLAIN:  one thread per particle; a warp runs as long as its largest 4^k.
 //  BINNED: one persistent kernel per macro step with an atomic work cursor.
-//          The bulk streams every particle with 128-bit loads; a particle whose
+//          The bulk streams every particle with coalesced evict-first loads
+//          (one particle per lane, two rounds in flight); a particle whose
 //          criterion gives k = 0 is pushed at once, one with k > 0 is compacted
 //          (warp match + one atomic per k) into the queue of its k and its
 //          sub-cycling is deferred.  The first work items of the next step's
@@ -85,8 +86,11 @@ void lagrange_monomials(int p, float (&mono)[2][kMaxOrder + 1][kMaxOrder + 1]) {
 // node, so an m = 1 push (and the criterion) that reads these two nodes and
 // applies the tent weight gets exactly the bits of the full gather, from two
 // loads per grid instead of 2(p+1).
+//
+// With coef set, the same pass also writes each node's monomial coefficients
+// (to_monomial over the same levels, so the same bits): E_y's p+1 then B_z's.
 template <int P>
-__global__ void halfstep_kernel(PushArgsMixed a, int64_t W, float* outE, float* outB) {
+__global__ void halfstep_kernel(PushArgsMixed a, int64_t W, float* outE, float* outB, float* coef) {
   constexpr int stride = 2 * (P + 1);
   const float* wB = a.wtab + a.crit_row * stride + (P + 1);
   const float* wE = a.wtab + wrow(0, 1) * stride;
@@ -103,19 +107,30 @@ __global__ void halfstep_kernel(PushArgsMixed a, int64_t W, float* outE, float* 
     }
     outE[c] = fe;
     outB[c] = fb;
+    if (coef) {
+      float e0[P + 1], e1[P + 1], b0[P + 1], b1[P + 1];
+      to_monomial<P>(F.E, (int32_t)c, (int32_t)c, a.mono[0], e0, e1);
+      to_monomial<P>(F.B, (int32_t)c, (int32_t)c, a.mono[1], b0, b1);
+      float* r = coef + c * stride;
+#pragma unroll
+      for (int q = 0; q <= P; ++q) {
+        r[q] = e0[q];
+        r[P + 1 + q] = b0[q];
+      }
+    }
   }
 }
 
 cudaError_t launch_halfstep(const PushArgsMixed& a, int order, int64_t W, float* outE, float* outB,
-                            cudaStream_t s) {
+                            float* coef, cudaStream_t s) {
   const int64_t want = (W + 255) / 256;
   const int blocks = (int)(want < 152 * 8 ? want : 152 * 8);
   switch (order) {
-    case 1: halfstep_kernel<1><<<blocks, 256, 0, s>>>(a, W, outE, outB); break;
-    case 2: halfstep_kernel<2><<<blocks, 256, 0, s>>>(a, W, outE, outB); break;
-    case 3: halfstep_kernel<3><<<blocks, 256, 0, s>>>(a, W, outE, outB); break;
-    case 4: halfstep_kernel<4><<<blocks, 256, 0, s>>>(a, W, outE, outB); break;
-    case 5: halfstep_kernel<5><<<blocks, 256, 0, s>>>(a, W, outE, outB); break;
+    case 1: halfstep_kernel<1><<<blocks, 256, 0, s>>>(a, W, outE, outB, coef); break;
+    case 2: halfstep_kernel<2><<<blocks, 256, 0, s>>>(a, W, outE, outB, coef); break;
+    case 3: halfstep_kernel<3><<<blocks, 256, 0, s>>>(a, W, outE, outB, coef); break;
+    case 4: halfstep_kernel<4><<<blocks, 256, 0, s>>>(a, W, outE, outB, coef); break;
+    case 5: halfstep_kernel<5><<<blocks, 256, 0, s>>>(a, W, outE, outB, coef); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -165,7 +180,7 @@ __global__ void __launch_bounds__(256) push_mixed_plain_kernel(PushArgsMixed a) 
     count_step(tc, sh, k, capped);
     bool ok = true;
     if (k == 0 && a.halfE) {
-      const float h_old = ldexpf(a.dt, -2 * (st & 0x7f));
+      const float h_old = pow4_down(a.dt, st & 0x7f);
       const float hp = __fmul_rn(0.5f, __fadd_rn(h_old, a.dt));
       boris_f32(half_lerp(a.halfE, je, we, a.mask), b0, hp, __fmul_rn(a.dt, a.inv_dx), a.qm, s);
     } else {
@@ -190,9 +205,14 @@ __global__ void __launch_bounds__(256) push_mixed_plain_kernel(PushArgsMixed a) 
 //     once unless k >= kDeferMin again).  Being first, the longest serial
 //     chains start as the launch starts and run beside the stream below.
 //  2. predicted items (predicted schedule only): particles binned before the
-//     launch by the predictor's k, pushed fully, largest k first.
-//  3. stream chunks of kChunk particles, one per thread, the next particle's
-//     state loaded while the current one is pushed.  k = 0: pushed at once (the
+//     launch by the predictor's k (k >= kDeferMin), largest k first.  Each
+//     takes its exact criterion; k = 0 and k = the predicted k are pushed at
+//     once (so a warp of right predictions is dense), any other k goes where
+//     the stream would send it (stash or deferral), so a wrong prediction
+//     costs one idle lane.
+//  3. stream chunks of kChunk particles, staged into shared memory tile by
+//     tile with bulk copies (one tile in flight while another is pushed),
+//     one particle per lane.  k = 0: pushed at once (the
 //     criterion's B_z serves the push).  k = 1, 2: parked in the warp's stash
 //     for that k (shared memory); whenever a stash holds 32 particles the warp
 //     pushes them together, so short sub-cycles never diverge a warp and never
@@ -203,51 +223,99 @@ __global__ void __launch_bounds__(256) push_mixed_plain_kernel(PushArgsMixed a) 
 // it), bits 4-6 = deferred k (0 = none), bit 7 = lost.
 
 // Before a predicted-schedule launch: particles the stream would take this
-// step and whose predicted k is > 0 go into the queue of that k, and their
+// step and whose predicted k is >= min_k go into the queue of that k, and their
 // parity bit is flipped so the stream leaves them to the predicted items.
 __global__ void bin_predicted_kernel(const uint8_t* pred, uint8_t* status, int64_t n,
-                                     int parity_cur, int32_t* pred_queue, int32_t* pred_count,
-                                     int64_t qcap) {
+                                     int parity_cur, int min_k, int32_t* pred_queue,
+                                     int32_t* pred_count, int64_t qcap) {
   const uint8_t want = parity_cur ? kParity : 0;
-  const int64_t n_round = (n + 31) & ~(int64_t)31;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_round;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int key = 0;
-    if (i < n) {
-      const uint8_t st = status[i];
-      const int kp = pred[i];
-      if (!(st & PIC_STATUS_LOST) && !(st & kDeferMask) && ((st & kParity) == want) && kp > 0 &&
-          kp <= 7) {
-        status[i] = (uint8_t)(st ^ kParity);
-        key = kp;
+  const int lane = threadIdx.x & 31;
+  // four particles per thread per pass (one 32-bit word of each byte array)
+  const int64_t n_words = (n + 3) / 4;
+  const int64_t w_round = (n_words + 31) & ~(int64_t)31;
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < w_round;
+       w += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = 4 * w;
+    uint32_t stw = 0, pw = 0;
+    if (i0 + 4 <= n) {
+      stw = reinterpret_cast<const uint32_t*>(status)[w];
+      pw = reinterpret_cast<const uint32_t*>(pred)[w];
+    } else {
+      for (int q = 0; q < 4; ++q)
+        if (i0 + q < n) {
+          stw |= (uint32_t)status[i0 + q] << (8 * q);
+          pw |= (uint32_t)pred[i0 + q] << (8 * q);
+        } else {
+          stw |= (uint32_t)PIC_STATUS_LOST << (8 * q);
+        }
+    }
+    int keys[4];
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint8_t st = (uint8_t)(stw >> (8 * q));
+      const int kp = (int)((pw >> (8 * q)) & 0xffu);
+      keys[q] = (!(st & PIC_STATUS_LOST) && !(st & kDeferMask) && ((st & kParity) == want) &&
+                 kp >= min_k && kp <= 7)
+                    ? kp
+                    : 0;
+      any |= keys[q] != 0;
+    }
+    if (!__any_sync(0xffffffffu, any)) continue;
+    uint32_t flip = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int key = keys[q];
+      if (!__any_sync(0xffffffffu, key != 0)) continue;
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      const int leader = __ffs(peers) - 1;
+      int base = 0;
+      if (key != 0 && lane == leader) base = atomicAdd(&pred_count[key], __popc(peers));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (key != 0) {
+        pred_queue[(int64_t)(key - 1) * qcap + base + __popc(peers & ((1u << lane) - 1u))] =
+            (int32_t)(i0 + q);
+        flip |= (uint32_t)kParity << (8 * q);
       }
     }
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(peers) - 1;
-    int base = 0;
-    if (key != 0 && lane == leader) base = atomicAdd(&pred_count[key], __popc(peers));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (key != 0)
-      pred_queue[(int64_t)(key - 1) * qcap + base + __popc(peers & ((1u << lane) - 1u))] = (int32_t)i;
+    if (flip) {
+      if (i0 + 4 <= n) {
+        reinterpret_cast<uint32_t*>(status)[w] = stw ^ flip;
+      } else {
+        for (int q = 0; q < 4; ++q)
+          if ((flip >> (8 * q)) & 0xffu) status[i0 + q] = (uint8_t)((stw ^ flip) >> (8 * q));
+      }
+    }
   }
 }
 
 cudaError_t launch_bin_predicted(const uint8_t* pred, uint8_t* status, int64_t n, int parity_cur,
-                                 int32_t* pred_queue, int32_t* pred_count, int64_t qcap,
+                                 int min_k, int32_t* pred_queue, int32_t* pred_count, int64_t qcap,
                                  cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  const int64_t want = (n + 255) / 256;
+  const int64_t want = (n + 1023) / 1024;
   const int blocks = (int)(want < 152 * 8 ? want : 152 * 8);
-  bin_predicted_kernel<<<blocks, 256, 0, s>>>(pred, status, n, parity_cur, pred_queue, pred_count,
-                                              qcap);
+  bin_predicted_kernel<<<blocks, 256, 0, s>>>(pred, status, n, parity_cur, min_k < 1 ? 1 : min_k,
+                                              pred_queue, pred_count, qcap);
   return cudaGetLastError();
 }
 
+// Dynamic shared memory of the binned kernel: the warps' stashes, then their
+// staged stream tiles.
+constexpr size_t kStashBytes = sizeof(Stash) * kWarps * kStashK;
+constexpr size_t kBinnedSmem = kStashBytes + sizeof(Tile) * kWarps * kStages;
+static_assert(kStashBytes % 128 == 0, "tiles start on a 128-byte boundary");
+
+#ifndef PIC_BINNED_MIN_BLOCKS
+#define PIC_BINNED_MIN_BLOCKS 3
+#endif
+
 template <int P, bool RING>
-__global__ void __launch_bounds__(kThreads, 3) push_binned_kernel(PushArgsMixed a) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__global__ void __launch_bounds__(kThreads, PIC_BINNED_MIN_BLOCKS) push_binned_kernel(PushArgsMixed a) {
+  extern __shared__ __align__(128) unsigned char smem[];
   Stash* stashes = reinterpret_cast<Stash*>(smem);  // [kWarps][kStashK]
+  Tile* tiles = reinterpret_cast<Tile*>(smem + kStashBytes);  // [kWarps][kStages]
+  __shared__ __align__(8) uint64_t bars[kWarps * kStages];
   __shared__ unsigned long long sh[12];
   __shared__ int s_task[kWarps];
   __shared__ long long heavy_end[8];  // deferred items per k, largest k first (cumulative)
@@ -279,6 +347,15 @@ __global__ void __launch_bounds__(kThreads, 3) push_binned_kernel(PushArgsMixed 
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   Stash* my_stash = stashes + warp * kStashK;
+  Tile* my_tiles = tiles + warp * kStages;
+  uint64_t* my_bars = bars + warp * kStages;
+  uint32_t phase = 0;  // bit s: parity of stage s's next completion
+  if (lane == 0) {
+#pragma unroll
+    for (int sidx = 0; sidx < kStages; ++sidx) mbar_init(my_bars + sidx);
+    mbar_init_fence();
+  }
+  __syncwarp();
   int stash_n[kStashK];
 #pragma unroll
   for (int q = 0; q < kStashK; ++q) stash_n[q] = 0;
@@ -290,12 +367,86 @@ __global__ void __launch_bounds__(kThreads, 3) push_binned_kernel(PushArgsMixed 
   const int64_t n_chunks = a.finalize ? 0 : (a.n + kChunk - 1) / kChunk;
   const int64_t n_items = n_pred_end + n_chunks;
 
-  for (;;) {
+  // park k = 1, 2 in the warp's stashes; push a stash when it holds 32
+  // (warp-collective; sk = 0: nothing to park)
+  auto park = [&](int sk, int32_t i, const MixedState& s, uint8_t k_prev) {
+#pragma unroll
+    for (int q = 0; q < kStashK; ++q) {
+      const unsigned m = __ballot_sync(0xffffffffu, sk == q + 1);
+      if (m == 0u) continue;
+      Stash& S = my_stash[q];
+      if (sk == q + 1) {
+        const int pos = stash_n[q] + __popc(m & ((1u << lane) - 1u));
+        S.idx[pos] = i;
+        S.cell[pos] = s.cell;
+        S.frac[pos] = s.frac;
+        S.ux[pos] = s.ux;
+        S.uy[pos] = s.uy;
+        S.uz[pos] = s.uz;
+        S.kp[pos] = k_prev;
+      }
+      stash_n[q] += __popc(m);
+      __syncwarp();
+      if (stash_n[q] >= 32) stash_drain<P, RING>(a, F, S, q + 1, stash_n[q], 32, sh);
+    }
+  };
+
+  // one stream particle: criterion, then push (k = 0), park (k = 1, 2) or
+  // defer (k >= kDeferMin).  Warp-collective.
+  auto stream_one = [&](int64_t i, uint8_t st, MixedState s) {
+    const bool mine = i < a.n && !(st & PIC_STATUS_LOST) && !(st & kDeferMask) &&
+                      ((st & kParity) == want);
+    int key = 0, sk = 0;
+    if (mine) {
+      int32_t je, jb;
+      float we, wb;
+      const bool inwin = tent_coords(s.cell, s.frac, F.lo, F.hi, je, we, jb, wb);
+      float b0, ey;
+      if (a.halfE) {
+        b0 = half_lerp(a.halfB, jb, wb, a.mask);
+        ey = half_lerp(a.halfE, je, we, a.mask);
+      } else {
+        b0 = gather_f32<P>(F.B, wcrit, jb, wb, a.mask);
+        ey = gather_f32<P>(F.E, w0, je, we, a.mask);
+      }
+      if (!inwin) {
+        a.status[i] = (uint8_t)(st | PIC_STATUS_LOST);
+        atomicAdd(&sh[11], 1ull);
+      } else {
+        bool capped;
+        const int k = psi_to_k(b0, s, a.qm_abs, a.dt, a.psi_max, a.k_max, capped);
+        count_step(tc, sh, k, capped);
+        const int k_prev = st & 7;
+        if (k == 0) {
+          const float h_old = pow4_down(a.dt, k_prev);
+          const float hp = __fmul_rn(0.5f, __fadd_rn(h_old, a.dt));
+          boris_f32(ey, b0, hp, hx0, a.qm, s);
+          normalize(s);
+          store_stream(a, i, s);
+          a.status[i] = done;
+        } else if (k < kDeferMin) {
+          sk = k;
+        } else {
+          a.status[i] = (uint8_t)(k_prev | (k << 4));
+          key = k;
+        }
+      }
+    }
+    enqueue(a, key, (int32_t)i);
+    park(sk, (int32_t)i, s, (uint8_t)(st & 7));
+  };
+
+  auto claim = [&]() -> int64_t {
     if (lane == 0) s_task[warp] = atomicAdd(a.cursor, 1);
     __syncwarp();
     const int64_t t = s_task[warp];
     __syncwarp();
-    if (t >= n_items) break;
+    return t;
+  };
+
+  // deferred and predicted items first (they come first in the cursor order)
+  int64_t t = claim();
+  while (t < n_pred_end) {
     if (t < n_heavy) {
       int k = 7;
       while (k > 1 && t >= heavy_end[k]) --k;
@@ -308,98 +459,106 @@ __global__ void __launch_bounds__(kThreads, 3) push_binned_kernel(PushArgsMixed 
         heavy_particle<P, RING>(a, Fp, F, wcrit, i, tc, sh, key);
       }
       enqueue(a, key, i);
-      continue;
-    }
-    if (t < n_pred_end) {
+    } else {
       int k = 7;
       while (k > 1 && t >= pred_end[k]) --k;
       const int64_t first = (k == 7 ? n_heavy : pred_end[k + 1]);
       const int64_t e = (t - first) * 32 + lane;
-      if (e < a.pred_count[k])
-        predicted_particle<P, RING>(a, F, wcrit, a.pred_queue[(int64_t)(k - 1) * a.qcap + e], tc, sh);
-      continue;
-    }
-    // stream chunk
-    const int64_t c0 = (t - n_pred_end) * kChunk;
-    int64_t i = c0 + lane;
-    uint8_t st = PIC_STATUS_LOST;
-    MixedState s = {0, 0.5f, 0.f, 0.f, 0.f};
-    if (i < a.n) {
-      st = a.status[i];
-      s = load_state(a, i);
-    }
-#pragma unroll 1
-    for (int r = 0; r < kChunk / 32; ++r, i += 32) {
-      const int64_t inext = i + 32;
-      uint8_t st_n = PIC_STATUS_LOST;
-      MixedState s_n = {0, 0.5f, 0.f, 0.f, 0.f};
-      if (r + 1 < kChunk / 32 && inext < a.n) {
-        st_n = a.status[inext];
-        s_n = load_state(a, inext);
-      }
-      const bool mine = i < a.n && !(st & PIC_STATUS_LOST) && !(st & kDeferMask) &&
-                        ((st & kParity) == want);
       int key = 0, sk = 0;
-      if (mine) {
-        int32_t je, jb;
-        float we, wb;
-        const bool inwin = tent_coords(s.cell, s.frac, F.lo, F.hi, je, we, jb, wb);
-        float b0, ey;
-        if (a.halfE) {
-          b0 = half_lerp(a.halfB, jb, wb, a.mask);
-          ey = half_lerp(a.halfE, je, we, a.mask);
-        } else {
-          b0 = gather_f32<P>(F.B, wcrit, jb, wb, a.mask);
-          ey = gather_f32<P>(F.E, w0, je, we, a.mask);
+      int32_t i = 0;
+      MixedState s = {0, 0.5f, 0.f, 0.f, 0.f};
+      uint8_t kp = 0;
+      if (e < a.pred_count[k]) {
+        i = a.pred_queue[(int64_t)(k - 1) * a.qcap + e];
+        predicted_particle<P, RING>(a, F, wcrit, i, k, tc, sh, key, sk, s, kp);
+      }
+      enqueue(a, key, i);
+      park(sk, i, s, kp);
+    }
+    t = claim();
+  }
+
+  // The stream: every later claim is a stream item of kChunk particles, taken
+  // as tiles of kTile.  Each warp keeps kStages tiles staged in shared memory:
+  // while one is pushed the next is in flight, across item boundaries.  Tiles
+  // that are not whole (the array's tail) or arrays that are not 16-byte
+  // aligned are read with plain loads instead.
+  if (t < n_items) {
+    const int64_t n_tiles = (a.n + kTile - 1) / kTile;
+    constexpr int64_t kTilesPerItem = kChunk / kTile;
+    int64_t gen_next = (t - n_pred_end) * kTilesPerItem;
+    int64_t gen_end = gen_next + kTilesPerItem < n_tiles ? gen_next + kTilesPerItem : n_tiles;
+    bool gen_done = false;
+    auto gen = [&]() -> int64_t {  // next tile of this warp, -1 when the stream is exhausted
+      if (gen_done) return -1;
+      if (gen_next >= gen_end) {
+        const int64_t it = claim();
+        if (it >= n_items) {
+          gen_done = true;
+          return -1;
         }
-        if (!inwin) {
-          a.status[i] = (uint8_t)(st | PIC_STATUS_LOST);
-          atomicAdd(&sh[11], 1ull);
+        gen_next = (it - n_pred_end) * kTilesPerItem;
+        gen_end = gen_next + kTilesPerItem < n_tiles ? gen_next + kTilesPerItem : n_tiles;
+      }
+      return gen_next++;
+    };
+    auto whole = [&](int64_t tile) { return a.tma && (tile + 1) * kTile <= a.n; };
+    const uint64_t policy = evict_first_policy();
+    auto issue = [&](int sidx, int64_t tile) {
+      if (tile >= 0 && whole(tile) && lane == 0)
+        tile_issue(a, my_tiles + sidx, my_bars + sidx, tile * kTile, policy);
+    };
+    int64_t q[kStages];
+#pragma unroll
+    for (int sidx = 0; sidx < kStages; ++sidx) {
+      q[sidx] = gen();
+      issue(sidx, q[sidx]);
+    }
+    bool stop = false;
+    while (!stop) {
+#pragma unroll
+      for (int sidx = 0; sidx < kStages; ++sidx) {
+        if (stop) break;
+        const int64_t tile = q[sidx];
+        if (tile < 0) {
+          stop = true;
+          break;
+        }
+        const int64_t first = tile * kTile;
+        if (whole(tile)) {
+          if (!mbar_wait(my_bars + sidx, (phase >> sidx) & 1u)) {
+            // the copies never completed: flag it, let the other stage's copy
+            // land (bounded), and leave the stream
+            if (lane == 0) atomicExch(&a.stats->error, 1);
+#pragma unroll
+            for (int o = 0; o < kStages; ++o)
+              if (o != sidx && q[o] >= 0 && whole(q[o])) mbar_wait(my_bars + o, (phase >> o) & 1u);
+            stop = true;
+            break;
+          }
+          phase ^= 1u << sidx;
+          const Tile& T = my_tiles[sidx];
+#pragma unroll 1
+          for (int r = 0; r < kTile / 32; ++r) {
+            const int j = r * 32 + lane;
+            stream_one(first + j, T.st[j], MixedState{T.cell[j], T.frac[j], T.px[j], T.py[j], T.pz[j]});
+          }
         } else {
-          bool capped;
-          const int k = psi_to_k(b0, s, a.qm_abs, a.dt, a.psi_max, a.k_max, capped);
-          count_step(tc, sh, k, capped);
-          const int k_prev = st & 7;
-          if (k == 0) {
-            const float h_old = ldexpf(a.dt, -2 * k_prev);
-            const float hp = __fmul_rn(0.5f, __fadd_rn(h_old, a.dt));
-            boris_f32(ey, b0, hp, hx0, a.qm, s);
-            normalize(s);
-            store_state(a, i, s);
-            a.status[i] = done;
-          } else if (k < kDeferMin) {
-            sk = k;
-          } else {
-            a.status[i] = (uint8_t)(k_prev | (k << 4));
-            key = k;
+#pragma unroll 1
+          for (int r = 0; r < kTile / 32; ++r) {
+            uint8_t st;
+            MixedState s;
+            fetch_stream(a, first + r * 32 + lane, st, s);
+            stream_one(first + r * 32 + lane, st, s);
           }
         }
+        __syncwarp();  // every lane is done with the stage before it is refilled
+        q[sidx] = gen();
+        issue(sidx, q[sidx]);
       }
-      enqueue(a, key, (int32_t)i);
-      // park k = 1, 2 in the warp's stashes; push a stash when it holds 32
-#pragma unroll
-      for (int q = 0; q < kStashK; ++q) {
-        const unsigned m = __ballot_sync(0xffffffffu, sk == q + 1);
-        if (m == 0u) continue;
-        Stash& S = my_stash[q];
-        if (sk == q + 1) {
-          const int pos = stash_n[q] + __popc(m & ((1u << lane) - 1u));
-          S.idx[pos] = (int32_t)i;
-          S.cell[pos] = s.cell;
-          S.frac[pos] = s.frac;
-          S.ux[pos] = s.ux;
-          S.uy[pos] = s.uy;
-          S.uz[pos] = s.uz;
-          S.kp[pos] = (uint8_t)(st & 7);
-        }
-        stash_n[q] += __popc(m);
-        __syncwarp();
-        if (stash_n[q] >= 32) stash_drain<P, RING>(a, F, S, q + 1, stash_n[q], 32, sh);
-      }
-      st = st_n;
-      s = s_n;
     }
   }
+
   // push what is left in the stashes
 #pragma unroll
   for (int q = 0; q < kStashK; ++q)
@@ -436,10 +595,7 @@ __global__ void reset_status_kernel(uint8_t* status, int64_t n) {
 
 // ---------------------------------------------------------------- predictor features
 
-// phi = (asinh|E|, asinh|B|, asinh p_x, asinh p_y, asinh p_z, log gamma) of each
-// particle after macro step n, with E and B at its position extrapolated to
-// t_{n+1} (theta = 3/2) from step n's levels: everything known before level
-// n+1 arrives.  Lost particles get zeros.
+// phi of every particle after macro step n (see particle_features).
 template <int P>
 __global__ void features_kernel(PushArgsMixed a, float* phi) {
   StepFields<P, true> F;
@@ -448,23 +604,8 @@ __global__ void features_kernel(PushArgsMixed a, float* phi) {
   lagrange_f32<P>(1.5f, w);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    const uint8_t st = a.status[i];
-    if (!(st & PIC_STATUS_LOST)) {
-      const MixedState s = load_state(a, i);
-      int32_t je, jb;
-      float we, wb;
-      if (tent_coords(s.cell, s.frac, F.lo, F.hi, je, we, jb, wb)) {
-        const float ey = gather_f32<P>(F.E, w, je, we, a.mask);
-        const float bz = gather_f32<P>(F.B, w + (P + 1), jb, wb, a.mask);
-        f[0] = asinhf(fabsf(ey));
-        f[1] = asinhf(fabsf(bz));
-      }
-      f[2] = asinhf(s.ux);
-      f[3] = asinhf(s.uy);
-      f[4] = asinhf(s.uz);
-      f[5] = 0.5f * log1pf(norm2(s.ux, s.uy, s.uz));
-    }
+    float f[6];
+    particle_features<P>(a, F, w, i, f);
 #pragma unroll
     for (int q = 0; q < 6; ++q) phi[i * 6 + q] = f[q];
   }
@@ -500,8 +641,6 @@ static cudaError_t launch_p(const PushArgsMixed& a, int schedule, int sm_count, 
   return cudaGetLastError();
 }
 
-constexpr size_t kStashBytes = sizeof(Stash) * kWarps * kStashK;
-
 template <int P, bool RING>
 static cudaError_t launch_binned_p(const PushArgsMixed& a, int sm_count, cudaStream_t main,
                                    int* launches) {
@@ -509,16 +648,16 @@ static cudaError_t launch_binned_p(const PushArgsMixed& a, int sm_count, cudaStr
   static int occ = 0;
   if (occ == 0) {
     cudaError_t e = cudaFuncSetAttribute(push_binned_kernel<P, RING>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStashBytes);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBinnedSmem);
     if (e != cudaSuccess) return e;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, push_binned_kernel<P, RING>, kThreads,
-                                                  kStashBytes);
+                                                  kBinnedSmem);
     if (occ < 1) occ = 1;
   }
   int64_t blocks = (int64_t)sms * occ;
   const int64_t items = (a.n + kChunk - 1) / kChunk;
   if (!a.finalize && blocks > (items + kWarps - 1) / kWarps + sms) blocks = (items + kWarps - 1) / kWarps + sms;
-  push_binned_kernel<P, RING><<<(int)blocks, kThreads, kStashBytes, main>>>(a);
+  push_binned_kernel<P, RING><<<(int)blocks, kThreads, kBinnedSmem, main>>>(a);
   int n = 1;
   if (a.finalize) {
     const int64_t want = (a.n + 255) / 256;
@@ -547,6 +686,7 @@ cudaError_t launch_binned_step(const PushArgsMixed& a, int order, int sm_count, 
                                int* launches) {
   if (a.n <= 0) return cudaSuccess;
   if (a.ringE) {
+    if (!a.coef || !a.coef_p) return cudaErrorInvalidValue;  // the ring form reads the node tables
     switch (order) {
       case 1: return launch_binned_p<1, true>(a, sm_count, main, launches);
       case 2: return launch_binned_p<2, true>(a, sm_count, main, launches);

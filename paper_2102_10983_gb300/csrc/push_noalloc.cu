@@ -90,6 +90,8 @@ extern "C" int pic_push_mixed_noalloc(const pic_params* prm, int64_t n_particles
     return fail(PIC_EINVAL, "pic_push_mixed_noalloc: NULL argument");
   if (!(prm->dt > 0) || !(prm->dx > 0) || !(prm->psi_max > 0) || !isfinite(prm->qm) || prm->qm == 0.0)
     return fail(PIC_EINVAL, "pic_push_mixed_noalloc: dt, dx, psi_max must be > 0 and qm != 0");
+  if (!((float)prm->dt >= 0x1p-100f && (float)prm->dt < 0x1p100f))
+    return fail(PIC_EINVAL, "pic_push_mixed_noalloc: the mixed form needs 2^-100 <= dt < 2^100");
   if (prm->order < 1 || prm->order > kMaxOrder || prm->k_max < 0 || prm->k_max > kMaxK ||
       (prm->field_time != 0 && prm->field_time != 1))
     return fail(PIC_EINVAL, "pic_push_mixed_noalloc: order 1..5, k_max 0..7, field_time 0/1");
@@ -145,6 +147,8 @@ extern "C" int pic_push_mixed_noalloc(const pic_params* prm, int64_t n_particles
   base.n = n_particles;
   base.cell = cell; base.frac = frac; base.px = px; base.py = py; base.pz = pz;
   base.status = status;
+  base.tma = (((uintptr_t)cell | (uintptr_t)frac | (uintptr_t)px | (uintptr_t)py | (uintptr_t)pz |
+               (uintptr_t)status) & 15) == 0;
   base.mask = (int32_t)(W - 1);
   base.dt = (float)prm->dt;
   base.psi_max = (float)prm->psi_max;

@@ -66,6 +66,7 @@ SIGNATURES = {
     "pic_launch_count": (ctypes.c_int64, [_VP]),
     "pic_last_error": (ctypes.c_char_p, [_VP]),
     "pic_features": (ctypes.c_int, [_VP, _I64, _VP]),
+    "pic_predict": (ctypes.c_int, [_VP, _VP, _I64, _VP]),
     "pic_attach_predictor": (ctypes.c_int, [_VP, _VP, _I32]),
     "pic_mlp_param_count": (ctypes.c_int, []),
     "pic_mlp_create": (ctypes.c_int, [ctypes.c_uint64, _VP, ctypes.POINTER(_VP)]),
@@ -290,6 +291,12 @@ class Predictor:
 
     def infer(self, phi, pred):
         _check(lib().pic_mlp_infer(self.h, phi.data_ptr(), int(phi.shape[0]), pred.data_ptr()))
+
+
+def predict(integ: "Integrator", net: "Predictor", n: int, pred):
+    """pic_predict: the network's class for every particle after macro step n
+    (features and inference in one pass)."""
+    _check(lib().pic_predict(integ.ctx, net.h, int(n), pred.data_ptr()), integ.ctx)
 
 
 def features(integ: "Integrator", n: int, phi):

@@ -72,12 +72,16 @@ def train(net: "native.Predictor", X, Y, iters: int = 600, lr: float = 2e-3, bat
     return losses
 
 
-def c1_style_training_set(n_electrons: int = 65536, steps: int = 400, seed: int = 6):
+def c1_style_training_set(n_electrons: int = 65536, steps: int = 400, seed: int = 6,
+                          keep_quiet: float = 1.0):
     """Pairs from at-rest electrons in a switched-on a0 = 100 wave at dt = lambda/75
-    (the test-particle configuration, in a smaller ensemble)."""
+    (the test-particle configuration, in a smaller ensemble).  By default every
+    pair is kept, so the classes come with their natural frequencies and the
+    network's argmax only leaves k = 0 when it is confident: the schedule bins
+    a particle on that prediction, and a false alarm costs work."""
     import math
     from .workloads import DT75
     wl = Workload(name="predictor_training", n_particles=n_electrons, a0=100.0, dt=DT75,
                   dx=DT75 / 0.99, psi_max=0.01, order=3, n_steps=steps, x_lo=0.0,
                   x_hi=4 * math.pi, seed=seed, window=512, lead=120)
-    return log_pairs(wl, steps)
+    return log_pairs(wl, steps, keep_quiet=keep_quiet)

@@ -128,6 +128,42 @@ def test_features_kernel_matches_definition():
     np.testing.assert_allclose(got[alive], want[alive], rtol=2e-5, atol=2e-4)
 
 
+@pytest.mark.parametrize("n", [4000, 37])
+def test_fused_prediction_equals_features_then_inference(n):
+    """pic_predict (features and inference in one kernel) gives exactly the
+    classes of pic_features followed by pic_mlp_infer, including ragged tails
+    of the 32-particle warp tiles, with a network trained a little so its
+    weights are not the initial ones."""
+    wl = W.Workload(name="fused", n_particles=n, a0=150.0, dt=W.DT75, dx=W.DT75 / 0.99,
+                    psi_max=0.01, order=3, n_steps=0, x_lo=0.0, x_hi=2 * math.pi,
+                    thermal_sigma=W.MAXWELL_10KEV_SIGMA, seed=5)
+    p = wl.order
+    integ = native.Integrator(wl.dt, wl.dx, wl.psi_max, order=p, precision=native.PIC_MIXED,
+                              capacity=wl.n_particles, window=wl.window, ring_levels=p + 2)
+    ini = wl.particles()
+    integ.pic_particles_write(ini.x, ini.px, ini.py, ini.pz)
+    E, B, i0 = wl.levels(-p, 40 + p)
+    for r in range(p):
+        integ.pic_fields_upload(r - p, i0[r], E[r], B[r])
+    for s in range(40):
+        integ.pic_fields_upload(s, i0[s + p], E[s + p], B[s + p])
+        integ.pic_push_step(s, 1, want_stats=False)
+    net = native.Predictor(seed=3)
+    phi_t, y_t = _batch(4096, 9)
+    for _ in range(20):
+        net.train_step(torch.as_tensor(phi_t, device="cuda"), torch.as_tensor(y_t, device="cuda"), 3e-3)
+    phi = torch.empty((n, 6), dtype=torch.float32, device="cuda")
+    native.features(integ, 39, phi)
+    want = torch.empty(n, dtype=torch.uint8, device="cuda")
+    net.infer(phi, want)
+    got = torch.full((n,), 255, dtype=torch.uint8, device="cuda")
+    native.predict(integ, net, 39, got)
+    torch.cuda.synchronize()
+    integ.close()
+    net.close()
+    assert torch.equal(got, want)
+
+
 def test_training_on_logged_pairs_learns_the_next_k():
     """Log (features after step n, k of step n+1) from a run of the integrator,
     train on the GPU, and predict held-out pairs: the network must beat the

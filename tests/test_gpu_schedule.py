@@ -93,3 +93,48 @@ def test_predicted_bitwise_equals_plain_even_with_an_untrained_network(every):
     assert list(sa.k_hist) == list(sb.k_hist)
     assert (sa.substeps, sa.n_star, sa.out_of_window) == (sb.substeps, sb.n_star, sb.out_of_window)
     net.close()
+
+
+def test_trained_predictor_gains_over_the_unbinned_method():
+    """What the network buys: the same steps of a 2M-electron slice of the
+    a0 = 150 Maxwellian workload (electrons in random order) with the
+    front among the electrons, timed
+    with the plain (unbinned) schedule and with the predicted schedule driven by
+    a network trained on pairs the integrator logged; same bits, and the
+    predicted schedule must be at least 1.5x faster.  Exact-k binning is timed
+    too, for the record."""
+    from paper_2102_10983_gb300 import predictor
+    X, Y, _ = predictor.c1_style_training_set(n_electrons=16384, steps=300)
+    net = native.Predictor(seed=1)
+    predictor.train(net, X, Y, iters=300)
+    # electrons in random order: the layout a thermal plasma has once it has mixed
+    wl = W.Workload(**{**W.C2.__dict__, "n_particles": 2_097_152, "seed": 8, "sort_x": False})
+    p, start, K = 3, 600, 60
+    E, B, i0 = wl.levels(-p, start + K + p)
+    ini = wl.particles()
+    results = {}
+    for name, sched in (("plain", native.PIC_SCHED_PLAIN), ("binned", native.PIC_SCHED_BINNED),
+                        ("predicted", native.PIC_SCHED_PREDICTED)):
+        integ = native.Integrator(wl.dt, wl.dx, wl.psi_max, order=p, precision=native.PIC_MIXED,
+                                  schedule=sched, capacity=wl.n_particles, window=wl.window,
+                                  ring_levels=start + K + p + 1)
+        if sched == native.PIC_SCHED_PREDICTED:
+            integ.attach_predictor(net, 4)
+        integ.pic_particles_write(ini.x, ini.px, ini.py, ini.pz)
+        for r in range(start + K + p):
+            integ.pic_fields_upload(r - p, i0[r], E[r], B[r])
+        integ.pic_push_step(0, start, want_stats=False)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        integ.pic_push_step(start, K, want_stats=False)
+        b.record()
+        torch.cuda.synchronize()
+        results[name] = (a.elapsed_time(b), integ.read_numpy())
+        integ.close()
+    for u, v in zip(results["plain"][1], results["predicted"][1]):
+        np.testing.assert_array_equal(u, v)
+    t_plain, t_bin, t_pred = (results[k][0] for k in ("plain", "binned", "predicted"))
+    print(f"ms per step: plain {t_plain / K:.3f} binned {t_bin / K:.3f} predicted {t_pred / K:.3f}")
+    assert t_plain / t_pred >= 1.5, (t_plain, t_bin, t_pred)
+    net.close()
