@@ -231,10 +231,17 @@ __device__ __forceinline__ void table_coefs(const float* coef, int g, int32_t a0
   constexpr int S = 2 * (P + 1);
   const float* r0 = coef + (int64_t)a0 * S + g * (P + 1);
   const float* r1 = coef + (int64_t)a1 * S + g * (P + 1);
+  if constexpr (P == 3) {  // rows of 8 floats: each half is one aligned 16-byte load
+    const float4 v0 = __ldg(reinterpret_cast<const float4*>(r0));
+    const float4 v1 = __ldg(reinterpret_cast<const float4*>(r1));
+    c0[0] = v0.x; c0[1] = v0.y; c0[2] = v0.z; c0[3] = v0.w;
+    c1[0] = v1.x; c1[1] = v1.y; c1[2] = v1.z; c1[3] = v1.w;
+  } else {
 #pragma unroll
-  for (int q = 0; q <= P; ++q) {
-    c0[q] = __ldg(r0 + q);
-    c1[q] = __ldg(r1 + q);
+    for (int q = 0; q <= P; ++q) {
+      c0[q] = __ldg(r0 + q);
+      c1[q] = __ldg(r1 + q);
+    }
   }
 }
 

@@ -228,64 +228,71 @@ __global__ void __launch_bounds__(256) push_mixed_plain_kernel(PushArgsMixed a) 
 __global__ void bin_predicted_kernel(const uint8_t* pred, uint8_t* status, int64_t n,
                                      int parity_cur, int min_k, int32_t* pred_queue,
                                      int32_t* pred_count, int64_t qcap) {
+  __shared__ int blk_cnt[8];   // this pass's binned particles per k (block-wide)
+  __shared__ int blk_base[8];  // their start in the queue of k
   const uint8_t want = parity_cur ? kParity : 0;
-  const int lane = threadIdx.x & 31;
-  // four particles per thread per pass (one 32-bit word of each byte array)
-  const int64_t n_words = (n + 3) / 4;
-  const int64_t w_round = (n_words + 31) & ~(int64_t)31;
-  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < w_round;
-       w += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i0 = 4 * w;
-    uint32_t stw = 0, pw = 0;
-    if (i0 + 4 <= n) {
-      stw = reinterpret_cast<const uint32_t*>(status)[w];
-      pw = reinterpret_cast<const uint32_t*>(pred)[w];
-    } else {
-      for (int q = 0; q < 4; ++q)
-        if (i0 + q < n) {
-          stw |= (uint32_t)status[i0 + q] << (8 * q);
-          pw |= (uint32_t)pred[i0 + q] << (8 * q);
-        } else {
-          stw |= (uint32_t)PIC_STATUS_LOST << (8 * q);
-        }
+  // Sixteen particles per thread per pass: one 16-byte load of each byte
+  // array, so enough bytes are in flight.  Passes with a binned particle
+  // (rare) reserve the block's queue slots with one global atomic per k.
+  const int64_t n_vec = (n + 15) / 16;
+  for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x; v0 < n_vec;
+       v0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = v0 + threadIdx.x;
+    const int64_t i0 = 16 * v;
+    uint32_t sw[4] = {0x80808080u, 0x80808080u, 0x80808080u, 0x80808080u};  // lost: skipped
+    uint32_t pw[4] = {0u, 0u, 0u, 0u};
+    if (i0 + 16 <= n) {
+      const uint4 a4 = reinterpret_cast<const uint4*>(status)[v];
+      const uint4 b4 = reinterpret_cast<const uint4*>(pred)[v];
+      sw[0] = a4.x; sw[1] = a4.y; sw[2] = a4.z; sw[3] = a4.w;
+      pw[0] = b4.x; pw[1] = b4.y; pw[2] = b4.z; pw[3] = b4.w;
+    } else if (i0 < n) {
+      for (int q = 0; q < 16 && i0 + q < n; ++q) {
+        const int sh8 = 8 * (q & 3);
+        sw[q >> 2] = (sw[q >> 2] & ~(0xffu << sh8)) | ((uint32_t)status[i0 + q] << sh8);
+        pw[q >> 2] |= (uint32_t)pred[i0 + q] << sh8;
+      }
     }
-    int keys[4];
+    int keys[16];
     bool any = false;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint8_t st = (uint8_t)(stw >> (8 * q));
-      const int kp = (int)((pw >> (8 * q)) & 0xffu);
+    for (int q = 0; q < 16; ++q) {
+      const uint8_t st = (uint8_t)(sw[q >> 2] >> (8 * (q & 3)));
+      const int kp = (int)((pw[q >> 2] >> (8 * (q & 3))) & 0xffu);
       keys[q] = (!(st & PIC_STATUS_LOST) && !(st & kDeferMask) && ((st & kParity) == want) &&
                  kp >= min_k && kp <= 7)
                     ? kp
                     : 0;
       any |= keys[q] != 0;
     }
-    if (!__any_sync(0xffffffffu, any)) continue;
-    uint32_t flip = 0;
+    if (!__syncthreads_or(any)) continue;
+    if (threadIdx.x < 8) blk_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    int off[16];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int key = keys[q];
-      if (!__any_sync(0xffffffffu, key != 0)) continue;
-      const unsigned peers = __match_any_sync(0xffffffffu, key);
-      const int leader = __ffs(peers) - 1;
-      int base = 0;
-      if (key != 0 && lane == leader) base = atomicAdd(&pred_count[key], __popc(peers));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if (key != 0) {
-        pred_queue[(int64_t)(key - 1) * qcap + base + __popc(peers & ((1u << lane) - 1u))] =
-            (int32_t)(i0 + q);
-        flip |= (uint32_t)kParity << (8 * q);
+    for (int q = 0; q < 16; ++q) off[q] = keys[q] ? atomicAdd(&blk_cnt[keys[q]], 1) : 0;
+    __syncthreads();
+    if (threadIdx.x > 0 && threadIdx.x < 8 && blk_cnt[threadIdx.x] > 0)
+      blk_base[threadIdx.x] = atomicAdd(&pred_count[threadIdx.x], blk_cnt[threadIdx.x]);
+    __syncthreads();
+    uint32_t flip[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+      if (keys[q]) {
+        pred_queue[(int64_t)(keys[q] - 1) * qcap + blk_base[keys[q]] + off[q]] = (int32_t)(i0 + q);
+        flip[q >> 2] |= (uint32_t)kParity << (8 * (q & 3));
       }
-    }
-    if (flip) {
-      if (i0 + 4 <= n) {
-        reinterpret_cast<uint32_t*>(status)[w] = stw ^ flip;
+    if (flip[0] | flip[1] | flip[2] | flip[3]) {
+      if (i0 + 16 <= n) {
+        reinterpret_cast<uint4*>(status)[v] =
+            make_uint4(sw[0] ^ flip[0], sw[1] ^ flip[1], sw[2] ^ flip[2], sw[3] ^ flip[3]);
       } else {
-        for (int q = 0; q < 4; ++q)
-          if ((flip >> (8 * q)) & 0xffu) status[i0 + q] = (uint8_t)((stw ^ flip) >> (8 * q));
+        for (int q = 0; q < 16 && i0 + q < n; ++q)
+          if ((flip[q >> 2] >> (8 * (q & 3))) & 0xffu)
+            status[i0 + q] = (uint8_t)((sw[q >> 2] ^ flip[q >> 2]) >> (8 * (q & 3)));
       }
     }
+    __syncthreads();  // blk_cnt / blk_base are reused by the next pass
   }
 }
 
@@ -293,7 +300,7 @@ cudaError_t launch_bin_predicted(const uint8_t* pred, uint8_t* status, int64_t n
                                  int min_k, int32_t* pred_queue, int32_t* pred_count, int64_t qcap,
                                  cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  const int64_t want = (n + 1023) / 1024;
+  const int64_t want = (n + 4095) / 4096;
   const int blocks = (int)(want < 152 * 8 ? want : 152 * 8);
   bin_predicted_kernel<<<blocks, 256, 0, s>>>(pred, status, n, parity_cur, min_k < 1 ? 1 : min_k,
                                               pred_queue, pred_count, qcap);
