@@ -88,7 +88,13 @@ typedef struct {
                          1: at the middle of the j-th sub-interval of
                             [t_n - dt/2, t_n + dt/2]                              */
   int32_t schedule;   /* PIC_SCHED_*                                             */
-  int32_t reserved[3];
+  int32_t heavy_budget; /* binned schedules: Boris sub-steps a long (k >= 3)
+                           sub-cycle may take per launch; the rest continues in
+                           the next launch while the particle runs behind the
+                           stream and then catches up (the same bits either
+                           way; a call finishes every particle).  0: 256;
+                           < 0: no limit                                      */
+  int32_t reserved[2];
 } pic_params;
 
 typedef struct {

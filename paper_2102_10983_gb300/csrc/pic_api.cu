@@ -42,6 +42,12 @@ struct pic_ctx {
   uint8_t* pred = nullptr;
   float* half = nullptr;  // mixed form: E_y, B_z of every window node at the step's t_n
   float* coef = nullptr;  // mixed form: per node monomial coefficients, two steps (parity of s)
+  // binned mixed form: resumable long sub-cycles (per particle: the step it is
+  // in and the sub-steps done), and a device copy of slot_i0 for the kernel
+  int32_t* lag_step = nullptr;
+  uint16_t* lag_j = nullptr;
+  int64_t* dslot_i0 = nullptr;
+  int32_t heavy_budget = 256;
   int32_t* pred_queue = nullptr;
   const pic_mlp* mlp = nullptr;
   int32_t predict_every = 1;
@@ -87,7 +93,7 @@ static void free_all(pic_ctx* c) {
   void* ptrs[] = {c->x, c->px, c->py, c->pz, c->cell, c->frac, c->fpx, c->fpy, c->fpz,
                   c->status, c->ringE, c->ringB, c->staging, c->wtab64, c->wtab32,
                   c->dstats, c->queue, c->qcount, c->pred, c->pred_queue, c->half,
-                  c->coef};
+                  c->coef, c->lag_step, c->lag_j, c->dslot_i0};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -95,10 +101,12 @@ static void free_all(pic_ctx* c) {
 // ---------------------------------------------------------------- small kernels
 
 // Write a window of W nodes starting at global node i0 into a ring slot,
-// circularly: node i goes to position i & (W-1).
+// circularly: node i goes to position i & (W-1).  dslot_i0 (optional): the
+// device copy of the slots' window origins, updated in stream order.
 template <typename T>
 __global__ void scatter_level_kernel(T* slotE, T* slotB, const double* Ey, const double* Bz,
-                                     int64_t i0, int64_t W) {
+                                     int64_t i0, int64_t W, int64_t* dslot_i0, int32_t slot) {
+  if (dslot_i0 && blockIdx.x == 0 && threadIdx.x == 0) dslot_i0[slot] = i0;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < W;
        c += (int64_t)gridDim.x * blockDim.x) {
     int64_t pos = (i0 + c) & (W - 1);
@@ -229,6 +237,10 @@ extern "C" int pic_create(const pic_params* prm, int64_t capacity, int64_t windo
     if (prm->schedule != PIC_SCHED_PLAIN) {
       A((void**)&c->queue, 2 * 7 * cap * 4);
       A((void**)&c->qcount, 64 * 4);
+      A((void**)&c->lag_step, cap * 4);
+      A((void**)&c->lag_j, cap * 2);
+      A((void**)&c->dslot_i0, (size_t)c->R * 8);
+      c->heavy_budget = prm->heavy_budget == 0 ? 256 : prm->heavy_budget;
     }
     if (prm->schedule == PIC_SCHED_PREDICTED) {
       A((void**)&c->pred, cap);
@@ -449,12 +461,13 @@ extern "C" int pic_fields_upload(pic_ctx* c, int64_t level, int64_t i0, const do
   if (c->prm.precision == PIC_FP64) {
     double* sE = (double*)c->ringE + (int64_t)slot * W;
     double* sB = (double*)c->ringB + (int64_t)slot * W;
-    scatter_level_kernel<double><<<blocks, 256, 0, c->stream>>>(sE, sB, e, b, i0, W);
+    scatter_level_kernel<double><<<blocks, 256, 0, c->stream>>>(sE, sB, e, b, i0, W, nullptr, 0);
   } else {
     for (int copy = 0; copy < 2; ++copy) {
       float* sE = (float*)c->ringE + ((int64_t)slot + (int64_t)copy * c->R) * W;
       float* sB = (float*)c->ringB + ((int64_t)slot + (int64_t)copy * c->R) * W;
-      scatter_level_kernel<float><<<blocks, 256, 0, c->stream>>>(sE, sB, e, b, i0, W);
+      scatter_level_kernel<float><<<blocks, 256, 0, c->stream>>>(
+          sE, sB, e, b, i0, W, copy == 0 ? c->dslot_i0 : nullptr, slot);
       ++c->launches;
     }
     CUDA_TRY(c, cudaGetLastError());
@@ -582,6 +595,14 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
     if (binned) {
       base.cursor = (int*)(c->qcount + 16);
       base.blocks_done = (unsigned*)(c->qcount + 18);
+      // deferred particles may run behind the stream within this call: the
+      // kernel finds any step's levels in the ring from the slots' origins
+      base.lag_step = c->lag_step;
+      base.lag_j = c->lag_j;
+      base.step0 = n;
+      base.heavy_budget = c->heavy_budget;
+      base.ring_R = c->R;
+      base.slot_i0 = c->dslot_i0;  // kept current by pic_fields_upload, in stream order
     }
   }
   for (int64_t j = 0; j < n_steps; ++j) {
@@ -624,6 +645,7 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
       if (e == cudaSuccess) e = launch_push_f64(a, p, c->stream, &launches);
     } else {
       PushArgsMixed a = base;
+      a.step_cur = s;
       fill_mixed(c, a, s, lo, hi, false);
       // this step's fields at t_n on every window node (the m = 1 pushes) and
       // its node coefficient table (the sub-cycles); the previous step's table
@@ -687,6 +709,7 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
           f.queue_out = c->queue + ((n_steps + 1) & 1) * qsz;
           f.qcount_out = c->qcount + ((n_steps + 1) & 1) * 8;
           f.finalize = 1;
+          f.step_cur = s + 1;   // bring every deferred particle to the end of step s
           f.coef_p = coef_cur;  // the deferred work finishes this (the last) step
           f.pred_queue = nullptr;
           f.pred_count = nullptr;

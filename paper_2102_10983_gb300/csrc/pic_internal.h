@@ -108,6 +108,18 @@ struct PushArgsMixed {
   int parity_cur, parity_next;
   int finalize;
   int tma;  // 1: the six particle arrays are 16-byte aligned (stream tiles by bulk copy)
+  // resumable long sub-cycles (ring form; lag_step == nullptr: every deferred
+  // step is finished by the next launch).  A deferred particle is in macro
+  // step step0 + lag_step[i] with lag_j[i] of its sub-steps done; a deferred
+  // item spends at most heavy_budget sub-steps of long (k >= kDeferMin)
+  // sub-cycles per launch and catches a lagging particle up with the stream.
+  int32_t* lag_step;
+  uint16_t* lag_j;
+  int64_t step0;          // first macro step of the call
+  int64_t step_cur;       // this launch's stream step (closing launch: last step + 1)
+  int32_t heavy_budget;   // <= 0: no limit
+  int32_t ring_R;         // ring slots (levels at slot level mod R, mirrored at + R)
+  const int64_t* slot_i0; // device copy of each slot's window origin
   // predicted schedule: electrons binned before the launch by predicted k
   // (per-k queues, qcap entries each), pushed by this launch in full
   const int32_t* pred_queue;

@@ -265,17 +265,22 @@ __device__ __forceinline__ float horner(const float* c, float u) {
 // coefficients come from
 // the step's node table (TABLE: F.coef, written by the half-step kernel), else
 // from the levels.
+//
+// Sub-steps j0+1 .. j1 of the m (j1 = -1: all of them): a sub-cycle can stop
+// after any sub-step and resume from the state it left (offset not yet
+// normalised) with the same bits as an uninterrupted one.
 template <int P, bool RING, bool TABLE = false>
 __device__ __forceinline__ bool subcycle_f32(const StepFields<P, RING>& F, const float* wtab,
                                              int32_t mask, float dt, float inv_dx, float qm,
                                              int field_time,
                                              const float (&mono)[2][kMaxOrder + 1][kMaxOrder + 1],
-                                             int k, int k_prev, float b0, MixedState& s) {
+                                             int k, int k_prev, float b0, MixedState& s,
+                                             int j0 = 0, int j1 = -1) {
   constexpr int stride = 2 * (P + 1);
   const float h = pow4_down(dt, k);
   const float h_old = pow4_down(dt, k_prev);
   const float hx = __fmul_rn(h, inv_dx);
-  float hp = __fmul_rn(0.5f, __fadd_rn(h_old, h));
+  float hp = j0 == 0 ? __fmul_rn(0.5f, __fadd_rn(h_old, h)) : h;
   if (k == 0) {
     const float* wr = wtab + wrow(0, 1) * stride;
     int32_t je, jb;
@@ -295,7 +300,8 @@ __device__ __forceinline__ bool subcycle_f32(const StepFields<P, RING>& F, const
   for (int q = 0; q <= P; ++q) ce0[q] = ce1[q] = cb0[q] = cb1[q] = 0.f;
   // floors of the offset on the two grids at the cached nodes (NaN: none yet)
   float fe = __int_as_float(0x7fc00000), fb = fe;
-  for (int j = 1; j <= m; ++j) {
+  const int j_end = j1 < 0 ? m : j1;
+  for (int j = j0 + 1; j <= j_end; ++j) {
     const float u = __fmaf_rn((float)(j - 1), inv_m, u1);
     const float f = s.frac;
     const float fbm = __fsub_rn(f, 0.5f);
@@ -574,6 +580,42 @@ __device__ __forceinline__ void particle_features(const PushArgsMixed& a, const 
   f[5] = 0.5f * log1pf(norm2(s.ux, s.uy, s.uz));
 }
 
+// Field view of macro step s from the mirrored ring and the device copy of
+// the slots' window origins (the host's step_slots / fill_mixed, on the GPU):
+// for a deferred particle that runs behind the stream.  No node table.
+template <int P>
+__device__ __forceinline__ StepFields<P, true> ring_step_fields(const PushArgsMixed& a, int64_t s) {
+  StepFields<P, true> F;
+  const int64_t R = a.ring_R;
+  const int64_t start = ((s - P) % R + R) % R;
+  F.E.base = a.ringE + start * a.lstride;
+  F.B.base = a.ringB + start * a.lstride;
+  F.E.lstride = (int32_t)a.lstride;
+  F.B.lstride = (int32_t)a.lstride;
+  F.coef = nullptr;
+  int64_t lo = INT64_MIN, hi = INT64_MAX;
+#pragma unroll
+  for (int l = 0; l <= P; ++l) {
+    const int64_t o = a.slot_i0[(start + l) % R];
+    lo = o > lo ? o : lo;
+    hi = o + a.lstride - 1 < hi ? o + a.lstride - 1 : hi;
+  }
+  F.lo = (int32_t)lo;
+  F.hi = (int32_t)hi;
+  return F;
+}
+
+// Marks particle i as deferred in step s with k (a long sub-cycle pending),
+// j of its sub-steps done.
+__device__ __forceinline__ void defer_mark(const PushArgsMixed& a, int64_t i, int k_prev, int k,
+                                           int64_t s, int j = 0) {
+  a.status[i] = (uint8_t)(k_prev | (k << 4));
+  if (a.lag_step) {
+    a.lag_step[i] = (int32_t)(s - a.step0);
+    a.lag_j[i] = (uint16_t)j;
+  }
+}
+
 // ---------------------------------------------------------------- binned schedule pieces
 
 constexpr int kThreads = 256;
@@ -651,57 +693,132 @@ __device__ __forceinline__ void stash_drain(const PushArgsMixed& a, const StepFi
   n = rest;
 }
 
-// Deferred item: finish the previous step of particle i, then take its
-// criterion for the current step (pushed at once if k < kDeferMin, else
-// deferred again).  finalize: only finish the deferred step (public status).
+// Deferred item: particle i is in a step before this launch's (a long
+// sub-cycle, possibly partly done).  Finish it -- and, if it ran behind the
+// stream, every step up to the previous one, taking each step's criterion --
+// spending at most heavy_budget sub-steps of long sub-cycles; then take the
+// criterion of the current step: pushed at once if k < kDeferMin, else
+// deferred again.  Out of budget: the particle stays deferred where it is
+// (offset not normalised) and resumes in the next launch.  finalize: bring it
+// to the end of the last step only (public status).
 template <int P, bool RING>
 __device__ __forceinline__ void heavy_particle(const PushArgsMixed& a, const StepFields<P, RING>& Fp,
-                                               const StepFields<P, RING>& Fc, const float* wcrit,
-                                               int64_t i, ThreadCounters& tc,
-                                               unsigned long long* sh, int& defer_key) {
+                                            const StepFields<P, RING>& Fc, const float* wcrit,
+                                            int64_t i, ThreadCounters& tc,
+                                            unsigned long long* sh, int& defer_key) {
   defer_key = 0;
   const uint8_t st = a.status[i];
-  const int k = deferred_k(st);
-  const int k_prev = st & 7;
+  int k = deferred_k(st);
+  int k_prev = st & 7;
   MixedState s = load_state(a, i);
-  const bool ok = subcycle_f32<P, RING, RING>(Fp, a.wtab, a.mask, a.dt, a.inv_dx, a.qm,
-                                              a.field_time, a.mono, k, k_prev, 0.f, s);
-  normalize(s);
-  if (!ok) {
-    store_state(a, i, s);
-    a.status[i] = (uint8_t)(k | PIC_STATUS_LOST);
-    atomicAdd(&sh[11], 1ull);
-    return;
+  int64_t si = a.step_cur - 1;  // the step the particle is in
+  int j0 = 0;                    // its sub-steps already done
+  bool lag = false;
+  if constexpr (RING) {
+    if (a.lag_step) {
+      si = a.step0 + a.lag_step[i];
+      j0 = a.lag_j[i];
+      lag = true;
+    }
   }
-  if (a.finalize) {
-    store_state(a, i, s);
-    a.status[i] = (uint8_t)k;
-    return;
-  }
-  int32_t je, jb;
-  float we, wb;
-  if (!tent_coords(s.cell, s.frac, Fc.lo, Fc.hi, je, we, jb, wb)) {
-    store_state(a, i, s);
-    a.status[i] = (uint8_t)(k | PIC_STATUS_LOST);
-    atomicAdd(&sh[11], 1ull);
-    return;
-  }
-  bool capped;
-  float b0;
-  const int kn = criterion_f32<P>(Fc.B, wcrit, jb, wb, a.mask, s, a.qm_abs, a.dt, a.psi_max,
-                                  a.k_max, capped, b0);
-  count_step(tc, sh, kn, capped);
-  if (kn < kDeferMin) {
-    const bool ok2 = subcycle_f32<P, RING, RING>(Fc, a.wtab, a.mask, a.dt, a.inv_dx, a.qm,
-                                                 a.field_time, a.mono, kn, k, b0, s);
+  int budget = lag && !a.finalize && a.heavy_budget > 0 ? a.heavy_budget : INT_MAX;
+  float b0 = 0.f;  // the criterion's B_z of step si (used when k = 0)
+  for (;;) {
+    // sub-steps j0+1 .. j1 of step si
+    const int m = 1 << (2 * k);
+    int j1 = m;
+    if (k >= kDeferMin && m - j0 > budget) j1 = j0 + budget;
+    bool ok;
+    if (si == a.step_cur - 1) {
+      ok = subcycle_f32<P, RING, RING>(Fp, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, a.field_time,
+                                       a.mono, k, k_prev, b0, s, j0, j1);
+    } else {
+      if constexpr (RING) {
+        const StepFields<P, true> Fs = ring_step_fields<P>(a, si);
+        ok = subcycle_f32<P, true, false>(Fs, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, a.field_time,
+                                          a.mono, k, k_prev, b0, s, j0, j1);
+      } else {
+        ok = false;  // unreachable: without the lag arrays si is always the previous step
+      }
+    }
+    if (k >= kDeferMin) budget -= j1 - j0;
+    if (!ok) {
+      store_state(a, i, s);
+      a.status[i] = (uint8_t)(k | PIC_STATUS_LOST);
+      atomicAdd(&sh[11], 1ull);
+      return;
+    }
+    if (j1 < m) {  // out of budget inside the sub-cycle: resume here next launch
+      store_state(a, i, s);
+      defer_mark(a, i, k_prev, k, si, j1);
+      defer_key = k;
+      return;
+    }
     normalize(s);
-    store_state(a, i, s);
-    a.status[i] = ok2 ? (uint8_t)(kn | (a.parity_next ? kParity : 0)) : (uint8_t)(kn | PIC_STATUS_LOST);
-    if (!ok2) atomicAdd(&sh[11], 1ull);
-  } else {
-    store_state(a, i, s);
-    a.status[i] = (uint8_t)(k | (kn << 4));
-    defer_key = kn;
+    if (si == a.step_cur - 1) {
+      if (a.finalize) {
+        store_state(a, i, s);
+        a.status[i] = (uint8_t)k;
+        return;
+      }
+      int32_t je, jb;
+      float we, wb;
+      if (!tent_coords(s.cell, s.frac, Fc.lo, Fc.hi, je, we, jb, wb)) {
+        store_state(a, i, s);
+        a.status[i] = (uint8_t)(k | PIC_STATUS_LOST);
+        atomicAdd(&sh[11], 1ull);
+        return;
+      }
+      bool capped;
+      const int kn = criterion_f32<P>(Fc.B, wcrit, jb, wb, a.mask, s, a.qm_abs, a.dt, a.psi_max,
+                                      a.k_max, capped, b0);
+      count_step(tc, sh, kn, capped);
+      if (kn < kDeferMin) {
+        const bool ok2 = subcycle_f32<P, RING, RING>(Fc, a.wtab, a.mask, a.dt, a.inv_dx, a.qm,
+                                                     a.field_time, a.mono, kn, k, b0, s);
+        normalize(s);
+        store_state(a, i, s);
+        a.status[i] = ok2 ? (uint8_t)(kn | (a.parity_next ? kParity : 0))
+                          : (uint8_t)(kn | PIC_STATUS_LOST);
+        if (!ok2) atomicAdd(&sh[11], 1ull);
+      } else {
+        store_state(a, i, s);
+        defer_mark(a, i, k, kn, a.step_cur);
+        defer_key = kn;
+      }
+      return;
+    }
+    // behind the stream: the next step's criterion, then its sub-cycle
+    if constexpr (RING) {
+      si += 1;
+      const StepFields<P, true> Fs = si == a.step_cur - 1 ? StepFields<P, true>{} : ring_step_fields<P>(a, si);
+      const int32_t lo = si == a.step_cur - 1 ? Fp.lo : Fs.lo;
+      const int32_t hi = si == a.step_cur - 1 ? Fp.hi : Fs.hi;
+      int32_t je, jb;
+      float we, wb;
+      if (!tent_coords(s.cell, s.frac, lo, hi, je, we, jb, wb)) {
+        store_state(a, i, s);
+        a.status[i] = (uint8_t)(k | PIC_STATUS_LOST);
+        atomicAdd(&sh[11], 1ull);
+        return;
+      }
+      bool capped;
+      const int kn = si == a.step_cur - 1
+                         ? criterion_f32<P>(Fp.B, wcrit, jb, wb, a.mask, s, a.qm_abs, a.dt,
+                                            a.psi_max, a.k_max, capped, b0)
+                         : criterion_f32<P>(Fs.B, wcrit, jb, wb, a.mask, s, a.qm_abs, a.dt,
+                                            a.psi_max, a.k_max, capped, b0);
+      count_step(tc, sh, kn, capped);
+      k_prev = k;
+      k = kn;
+      j0 = 0;
+      if (k >= kDeferMin && budget <= 0) {
+        store_state(a, i, s);
+        defer_mark(a, i, k_prev, k, si);
+        defer_key = k;
+        return;
+      }
+    }
   }
 }
 
@@ -740,7 +857,7 @@ __device__ __forceinline__ void predicted_particle(const PushArgsMixed& a, const
   } else if (k < kDeferMin) {
     sk = k;
   } else {
-    a.status[i] = (uint8_t)(k_prev | (k << 4));
+    defer_mark(a, i, k_prev, k, a.step_cur);
     key = k;
   }
 }

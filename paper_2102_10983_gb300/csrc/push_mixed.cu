@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(kThreads, PIC_BINNED_MIN_BLOCKS) push_binned_k
         } else if (k < kDeferMin) {
           sk = k;
         } else {
-          a.status[i] = (uint8_t)(k_prev | (k << 4));
+          defer_mark(a, i, k_prev, k, a.step_cur);
           key = k;
         }
       }

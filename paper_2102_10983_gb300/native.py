@@ -29,7 +29,8 @@ class PicParams(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("dx", ctypes.c_double), ("psi_max", ctypes.c_double),
                 ("qm", ctypes.c_double), ("order", ctypes.c_int32), ("k_max", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("field_time", ctypes.c_int32),
-                ("schedule", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("schedule", ctypes.c_int32), ("heavy_budget", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class PicEnsemble(ctypes.Structure):
@@ -164,9 +165,10 @@ class Integrator:
 
     def __init__(self, dt, dx, psi_max, order=3, k_max=7, precision=PIC_FP64, field_time=0,
                  schedule=PIC_SCHED_PLAIN, qm=-1.0, capacity=0, window=256, ring_levels=None,
-                 stream=None):
+                 stream=None, heavy_budget=0):
         self.params = PicParams(float(dt), float(dx), float(psi_max), float(qm), int(order),
-                                int(k_max), int(precision), int(field_time), int(schedule))
+                                int(k_max), int(precision), int(field_time), int(schedule),
+                                int(heavy_budget))
         self.window = int(window)
         self.ring_levels = int(ring_levels if ring_levels is not None else order + 1)
         self.capacity = int(capacity)

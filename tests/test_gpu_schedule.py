@@ -29,10 +29,10 @@ def _wl(n, **kw):
     return W.Workload(**base)
 
 
-def _run(wl, schedule, n_steps, call_lens, order=3):
+def _run(wl, schedule, n_steps, call_lens, order=3, heavy_budget=0):
     integ = native.Integrator(wl.dt, wl.dx, wl.psi_max, order=order, precision=native.PIC_MIXED,
                               schedule=schedule, capacity=wl.n_particles, window=wl.window,
-                              ring_levels=order + 2 + max(call_lens))
+                              ring_levels=order + 2 + max(call_lens), heavy_budget=heavy_budget)
     ini = wl.particles()
     integ.pic_particles_write(ini.x, ini.px, ini.py, ini.pz)
     st = H.run_gpu_calls(integ, wl, order, 0, n_steps, call_lens)
@@ -55,11 +55,29 @@ def test_binned_bitwise_equals_plain(call_lens, n):
            (sb.substeps, sb.n_star, sb.clamped, sb.out_of_window)
 
 
+@pytest.mark.parametrize("budget", [5, 64, -1])
+@pytest.mark.parametrize("call_lens", [[1], [9, 90, 40]])
+def test_binned_resumable_long_subcycles_are_bitwise_plain(budget, call_lens):
+    """With a budget of a few sub-steps per launch the electrons the front hits
+    (k up to 5: 1,024 sub-steps) stop in the middle of their sub-cycles, run
+    many steps behind the stream and catch up; the results, counters and k of
+    every step stay the plain schedule's."""
+    wl = _wl(3000)
+    a, sa = _run(wl, native.PIC_SCHED_PLAIN, 1000, call_lens)
+    b, sb = _run(wl, native.PIC_SCHED_BINNED, 1000, call_lens, heavy_budget=budget)
+    assert sa.k_hist[5] > 0
+    for u, v in zip(a, b):
+        np.testing.assert_array_equal(u, v)
+    assert list(sa.k_hist) == list(sb.k_hist)
+    assert (sa.substeps, sa.n_star, sa.clamped, sa.out_of_window) == \
+           (sb.substeps, sb.n_star, sb.clamped, sb.out_of_window)
+
+
 @pytest.mark.parametrize("order", [1, 5])
 def test_binned_bitwise_other_orders_and_window_exit(order):
     wl = _wl(1000, lead=60, window=256)   # a short window: some electrons leave it
     a, sa = _run(wl, native.PIC_SCHED_PLAIN, 600, [50], order=order)
-    b, sb = _run(wl, native.PIC_SCHED_BINNED, 600, [50], order=order)
+    b, sb = _run(wl, native.PIC_SCHED_BINNED, 600, [50], order=order, heavy_budget=7)
     for u, v in zip(a, b):
         np.testing.assert_array_equal(u, v)
     assert sa.out_of_window == sb.out_of_window
