@@ -195,10 +195,11 @@ int pic_features(pic_ctx* ctx, int64_t n, float* phi);
 typedef struct pic_mlp pic_mlp;
 
 /* Attach a predictor to a PIC_SCHED_PREDICTED context: every `every` steps of
- * pic_push_step, the features after the previous step go through the network
- * and its predicted k bins the particles before the next launch (predictions
- * are reused in between).  The predictor must outlive its use by the context.
- * Errors: PIC_EINVAL. */
+ * pic_push_step (and at the first step of each call), the features after the
+ * previous step go through the network and the particles it predicts to take
+ * k >= 3 are binned by that k into a queue that the launches of the next
+ * `every` steps push ahead of the stream.  The predictor must outlive its use
+ * by the context.  Errors: PIC_EINVAL. */
 int pic_attach_predictor(pic_ctx* ctx, pic_mlp* mlp, int32_t every);
 
 /* Number of packed FP32 parameters (5128). */

@@ -262,7 +262,10 @@ __device__ __forceinline__ void infer_tiles2(const SmemW& s, const uint32_t (&x0
 // The same predictions as the features kernel followed by mlp_infer_kernel,
 // without the 24 bytes per particle of features going through HBM.
 template <int P>
-__global__ void __launch_bounds__(128) predict_kernel(PushArgsMixed a, const float* Pm,
+#ifndef PIC_PREDICT_MIN_BLOCKS
+#define PIC_PREDICT_MIN_BLOCKS 1
+#endif
+__global__ void __launch_bounds__(128, PIC_PREDICT_MIN_BLOCKS) predict_kernel(PushArgsMixed a, const float* Pm,
                                                       uint8_t* pred) {
   __shared__ SmemW s;
   __shared__ float ft[4][32][8];

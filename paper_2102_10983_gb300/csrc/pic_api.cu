@@ -227,7 +227,7 @@ extern "C" int pic_create(const pic_params* prm, int64_t capacity, int64_t windo
     if (e == cudaSuccess) e = cudaMalloc(p, bytes);
   };
   if (mixed) {
-    A((void**)&c->half, 2 * (size_t)window_cells * 4);
+    A((void**)&c->half, 2 * ((size_t)window_cells + 1) * 4);  // E_y, B_z: W + 1 nodes each
     A((void**)&c->coef, 2 * (size_t)window_cells * 2 * (prm->order + 1) * 4);
     A((void**)&c->cell, cap * 4);
     A((void**)&c->frac, cap * 4);
@@ -653,11 +653,11 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
       const int64_t coef_stride = W * 2 * (p + 1);
       float* coef_cur = c->coef + (s & 1) * coef_stride;
       float* coef_prev = c->coef + ((s - 1) & 1) * coef_stride;
-      e = launch_halfstep(a, p, W, c->half, c->half + W, coef_cur, c->stream);
+      e = launch_halfstep(a, p, W, c->half, c->half + W + 1, coef_cur, c->stream);
       ++launches;
       if (e != cudaSuccess) return fail(c, PIC_ECUDA, "half-step launch: %s", cudaGetErrorString(e));
       a.halfE = c->half;
-      a.halfB = c->half + W;
+      a.halfB = c->half + W + 1;
       a.coef = coef_cur;
       a.coef_p = j > 0 ? coef_prev : coef_cur;
       if (binned) {
@@ -678,22 +678,28 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
         a.parity_next = (int)((j + 1) & 1);
         a.finalize = 0;
         e = cudaSuccess;
-        if (predicted) {
-          // refresh the predictions from the state after the previous step
+        if (predicted && j % c->predict_every == 0) {
+          // refresh the predictions from the state after the previous step and
+          // rebuild the predicted queue, which the next predict_every steps
+          // push (a call starts with a refresh: its status bytes carry no
+          // queue marks)
+          e = cudaMemsetAsync(c->qcount + 32, 0, 8 * sizeof(int32_t), c->stream);
           int ps[kMaxOrder + 1];
           int64_t plo, phi;
-          if (j % c->predict_every == 0 && step_slots(c, s - 1, ps, &plo, &phi) == PIC_OK) {
+          if (e == cudaSuccess && step_slots(c, s - 1, ps, &plo, &phi) == PIC_OK) {
             PushArgsMixed fa = a;
             fill_mixed(c, fa, s - 1, plo, phi, false);
             fa.coef = fa.coef_p = nullptr;
             e = launch_predict_fused(fa, p, mlp_device_params(c->mlp), c->pred, c->sm_count,
                                      c->stream);
             ++launches;
+            if (e == cudaSuccess)
+              e = launch_bin_predicted(c->pred, c->status, c->n, a.parity_cur, kDeferMin,
+                                       c->pred_queue, c->qcount + 32, c->capacity, c->stream);
+            ++launches;
           }
-          if (e == cudaSuccess)
-            e = launch_bin_predicted(c->pred, c->status, c->n, a.parity_cur, kDeferMin, c->pred_queue,
-                                     c->qcount + 32, c->capacity, c->stream);
-          ++launches;
+        }
+        if (predicted) {
           a.pred_queue = c->pred_queue;
           a.pred_count = c->qcount + 32;
         }

@@ -76,7 +76,8 @@ struct PushArgsMixed {
   const float* Ep[kMaxOrder + 1];  // previous step's levels (binned: deferred work)
   const float* Bp[kMaxOrder + 1];
   // E_y and B_z of every window node interpolated to t_n (theta = 1/2), written
-  // by the step's half-step kernel; nullptr = not provided (gather the levels)
+  // by the step's half-step kernel, W + 1 nodes each (node W repeats node 0);
+  // nullptr = not provided (gather the levels)
   const float* halfE;
   const float* halfB;
   // per window node, the monomial coefficients of the temporal interpolant of
@@ -120,10 +121,11 @@ struct PushArgsMixed {
   int32_t heavy_budget;   // <= 0: no limit
   int32_t ring_R;         // ring slots (levels at slot level mod R, mirrored at + R)
   const int64_t* slot_i0; // device copy of each slot's window origin
-  // predicted schedule: electrons binned before the launch by predicted k
-  // (per-k queues, qcap entries each), pushed by this launch in full
+  // predicted schedule: electrons binned by predicted k at the last refresh of
+  // the predictions (per-k queues, qcap entries each), marked in their status
+  // byte; every launch until the next refresh pushes those still marked
   const int32_t* pred_queue;
-  int32_t* pred_count;  // [8], zeroed by this launch's last block
+  int32_t* pred_count;  // [8], set by the refresh's binning pass
 };
 
 // Fills PushArgsMixed::mono for order p (host side, FP64 expansion).
@@ -202,8 +204,9 @@ cudaError_t launch_halfstep(const PushArgsMixed& a, int order, int64_t W, float*
                             float* coef, cudaStream_t s);
 cudaError_t launch_features_mixed(const PushArgsMixed& a, int order, float* phi, cudaStream_t s);
 
-// Bins the particles whose predicted k is >= min_k (and that the stream would
-// take this step) into per-k queues.
+// Rebuilds the predicted queue: clears the old queue's marks, then bins and
+// marks the particles whose predicted k is >= min_k (and that the stream would
+// take this step) into per-k queues; pred_count must be zero on entry.
 cudaError_t launch_bin_predicted(const uint8_t* pred, uint8_t* status, int64_t n, int parity_cur,
                                  int min_k, int32_t* pred_queue, int32_t* pred_count, int64_t qcap,
                                  cudaStream_t s);

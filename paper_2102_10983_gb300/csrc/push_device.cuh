@@ -60,7 +60,7 @@ __device__ __forceinline__ bool tent_coords(int32_t cell, float f, int32_t lo, i
   we = __fsub_rn(f, fe);
   jb = cell + (int32_t)fb;
   wb = __fsub_rn(fbm, fb);
-  return je >= lo && je < hi && jb >= lo && jb < hi;
+  return jb >= lo && je < hi;  // jb <= je: both nodes of both grids in [lo, hi)
 }
 
 __device__ __forceinline__ float norm2(float a, float b, float c) {
@@ -72,12 +72,19 @@ __device__ __forceinline__ float norm2(float a, float b, float c) {
 // square root and no division: Psi0 <= Psi_max 4^k  <=>
 // (|q/m| dt B)^2 <= (2 Psi_max)^2 (1 + |p|^2) 16^k, and the right side is
 // scaled by 16 (exactly) per step of k.
+// The two sides of the k = 0 test: a2 = (|q/m| dt B)^2, rhs = (2 Psi_max)^2 (1 + |p|^2).
+__device__ __forceinline__ void psi_terms(float b0, const MixedState& s, float qm_abs, float dt,
+                                          float psi_max, float& a2, float& rhs) {
+  const float a = __fmul_rn(__fmul_rn(qm_abs, dt), b0);
+  a2 = __fmul_rn(a, a);
+  const float tp = __fmul_rn(2.0f, psi_max);
+  rhs = __fmul_rn(__fmul_rn(tp, tp), __fadd_rn(1.0f, norm2(s.ux, s.uy, s.uz)));
+}
+
 __device__ __forceinline__ int psi_to_k(float b0, const MixedState& s, float qm_abs, float dt,
                                         float psi_max, int k_max, bool& capped) {
-  const float a = __fmul_rn(__fmul_rn(qm_abs, dt), b0);
-  const float a2 = __fmul_rn(a, a);
-  const float tp = __fmul_rn(2.0f, psi_max);
-  float rhs = __fmul_rn(__fmul_rn(tp, tp), __fadd_rn(1.0f, norm2(s.ux, s.uy, s.uz)));
+  float a2, rhs;
+  psi_terms(b0, s, qm_abs, dt, psi_max, a2, rhs);
   int k = 0;
   while (a2 > rhs && k < k_max) {
     rhs = __fmul_rn(rhs, 16.0f);
@@ -301,13 +308,18 @@ __device__ __forceinline__ bool subcycle_f32(const StepFields<P, RING>& F, const
   // floors of the offset on the two grids at the cached nodes (NaN: none yet)
   float fe = __int_as_float(0x7fc00000), fb = fe;
   const int j_end = j1 < 0 ? m : j1;
+  // u_j = u_1 + (j-1)/m: every partial sum is a multiple of 1/m in [-1, 1],
+  // exact in FP32, so the running sum has the bits of the direct formula
+  float u = __fmaf_rn((float)j0, inv_m, u1);
   for (int j = j0 + 1; j <= j_end; ++j) {
-    const float u = __fmaf_rn((float)(j - 1), inv_m, u1);
     const float f = s.frac;
     const float fbm = __fsub_rn(f, 0.5f);
-    if (!(f >= fe && f < __fadd_rn(fe, 1.0f) && fbm >= fb && fbm < __fadd_rn(fb, 1.0f))) {
+    float we = __fsub_rn(f, fe), wb = __fsub_rn(fbm, fb);
+    // cached nodes still hold iff both rounded weights lie in [+0, 1): then
+    // f - fe and fbm - fb are exact and fe, fb are the floors (a NaN or a
+    // negative weight fails the unsigned test)
+    if (!(__float_as_uint(we) < 0x3f800000u && __float_as_uint(wb) < 0x3f800000u)) {
       int32_t je, jb;
-      float we, wb;
       if (!tent_coords(s.cell, f, F.lo, F.hi, je, we, jb, wb)) return false;
       fe = floorf(f);
       fb = floorf(fbm);
@@ -326,14 +338,53 @@ __device__ __forceinline__ bool subcycle_f32(const StepFields<P, RING>& F, const
           to_monomial<P>(F.B, jb & mask, (jb + 1) & mask, mono[1], cb0, cb1);
       }
     }
-    const float we = __fsub_rn(f, fe), wb = __fsub_rn(fbm, fb);
     const float fe0 = horner<P>(ce0, u), fe1 = horner<P>(ce1, u);
     const float fb0 = horner<P>(cb0, u), fb1 = horner<P>(cb1, u);
     boris_f32(__fmaf_rn(we, __fsub_rn(fe1, fe0), fe0), __fmaf_rn(wb, __fsub_rn(fb1, fb0), fb0), hp,
               hx, qm, s);
     hp = h;
+    u = __fadd_rn(u, inv_m);
   }
   return true;
+}
+
+// The node-table form of subcycle_f32 behind one call site.  With
+// PIC_SUBCYCLE_NOINLINE defined, every caller in a kernel shares one copy of
+// its code (a call per sub-cycle instead of a copy per caller: less for the
+// instruction cache to hold); otherwise it is inlined at each caller.
+struct SubOut {
+  MixedState s;
+  bool ok;
+};
+template <int P>
+__device__ __noinline__ SubOut subcycle_table_call(StepFields<P, true> F, const float* wtab,
+                                                   int32_t mask, float dt, float inv_dx, float qm,
+                                                   int field_time, int k, int k_prev, float b0,
+                                                   MixedState s, int j0, int j1) {
+  float no_mono[2][kMaxOrder + 1][kMaxOrder + 1];  // the table form never reads it
+  SubOut o;
+  o.s = s;
+  o.ok = subcycle_f32<P, true, true>(F, wtab, mask, dt, inv_dx, qm, field_time, no_mono, k, k_prev,
+                                     b0, o.s, j0, j1);
+  return o;
+}
+template <int P, bool RING, bool TABLE>
+__device__ __forceinline__ bool subcycle_site(const StepFields<P, RING>& F, const float* wtab,
+                                              int32_t mask, float dt, float inv_dx, float qm,
+                                              int field_time,
+                                              const float (&mono)[2][kMaxOrder + 1][kMaxOrder + 1],
+                                              int k, int k_prev, float b0, MixedState& s,
+                                              int j0 = 0, int j1 = -1) {
+#ifdef PIC_SUBCYCLE_NOINLINE
+  if constexpr (RING && TABLE) {
+    const SubOut o = subcycle_table_call<P>(F, wtab, mask, dt, inv_dx, qm, field_time, k, k_prev, b0,
+                                            s, j0, j1);
+    s = o.s;
+    return o.ok;
+  }
+#endif
+  return subcycle_f32<P, RING, TABLE>(F, wtab, mask, dt, inv_dx, qm, field_time, mono, k, k_prev,
+                                      b0, s, j0, j1);
 }
 
 __device__ __forceinline__ void normalize(MixedState& s) {
@@ -344,30 +395,26 @@ __device__ __forceinline__ void normalize(MixedState& s) {
 
 // ---------------------------------------------------------------- counters
 
-// Per-thread counters in registers: steps with k = 0, 1, 2 (the common ones),
-// caps, sub-step sums.  Steps with k >= 3 are rare and go straight into the
-// block's shared counters.  (Shared-memory atomics on one address for every
-// sub-cycled particle serialised the warps at a front.)
+// Per-thread counters in registers: steps with k = 0, 1, 2 (the common ones)
+// and caps.  Steps with k >= 3 are rare and go straight into the block's
+// shared counters.  (Shared-memory atomics on one address for every
+// sub-cycled particle serialised the warps at a front.)  The sub-step sums are
+// not counted per particle: every counted step takes m = 4^k sub-steps, so
+// they follow from the k histogram when the block flushes.
 struct ThreadCounters {
   unsigned k0 = 0, k1 = 0, k2 = 0, capped = 0;
-  unsigned long long sub = 0, star = 0;
 };
 
 __device__ __forceinline__ void count_step(ThreadCounters& tc, unsigned long long* sh, int k,
                                            bool capped) {
-  const unsigned long long m = 1ull << (2 * k);
-  tc.sub += m;
-  if (k == 0) {
+  if (k == 0)
     ++tc.k0;
-  } else {
-    tc.star += m;
-    if (k == 1)
-      ++tc.k1;
-    else if (k == 2)
-      ++tc.k2;
-    else
-      atomicAdd(&sh[k], 1ull);
-  }
+  else if (k == 1)
+    ++tc.k1;
+  else if (k == 2)
+    ++tc.k2;
+  else
+    atomicAdd(&sh[k], 1ull);
   tc.capped += capped ? 1u : 0u;
 }
 
@@ -377,23 +424,27 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
   return v;
 }
 
-// All threads of the block must call this.
+// All threads of the block must call this.  Block counters: sh[0..7] the k
+// histogram, sh[10] caps, sh[11] particles lost; sh[8], sh[9] unused.
 __device__ __forceinline__ void flush_counters(const ThreadCounters& tc, unsigned long long* sh,
                                                DevStats* st) {
   const unsigned long long k0 = warp_sum(tc.k0), k1 = warp_sum(tc.k1), k2 = warp_sum(tc.k2);
   const unsigned long long cap = warp_sum(tc.capped);
-  const unsigned long long sub = warp_sum(tc.sub), star = warp_sum(tc.star);
   if ((threadIdx.x & 31) == 0) {
     if (k0) atomicAdd(&sh[0], k0);
     if (k1) atomicAdd(&sh[1], k1);
     if (k2) atomicAdd(&sh[2], k2);
-    if (sub) atomicAdd(&sh[8], sub);
-    if (star) atomicAdd(&sh[9], star);
     if (cap) atomicAdd(&sh[10], cap);
   }
   __syncthreads();
   if (threadIdx.x < 12) {
-    const unsigned long long v = sh[threadIdx.x];
+    unsigned long long v = 0;
+    if (threadIdx.x == 8 || threadIdx.x == 9) {  // sum of m = 4^k over the counted steps
+#pragma unroll
+      for (int k = threadIdx.x == 8 ? 0 : 1; k < 8; ++k) v += sh[k] << (2 * k);
+    } else {
+      v = sh[threadIdx.x];
+    }
     if (v) {
       unsigned long long* dst = threadIdx.x < 8 ? &st->k_hist[threadIdx.x]
                                 : threadIdx.x == 8 ? &st->substeps
@@ -426,11 +477,12 @@ __device__ __forceinline__ void store_state(const PushArgsMixed& a, int64_t i, c
 // The stream's loads and stores: each state word is touched once per step and
 // the whole state is larger than L2, so these are marked evict-first to leave
 // L2 to the field levels, half-step fields and queues.
-__device__ __forceinline__ void fetch_stream(const PushArgsMixed& a, int64_t i, uint8_t& st,
+// (Particle indices are below 2^31: 32-bit offsets address every array.)
+__device__ __forceinline__ void fetch_stream(const PushArgsMixed& a, uint32_t i, uint8_t& st,
                                              MixedState& s) {
   st = PIC_STATUS_LOST;
   s = {0, 0.5f, 0.f, 0.f, 0.f};
-  if (i < a.n) {
+  if ((int64_t)i < a.n) {
     st = __ldcs(a.status + i);
     s.cell = __ldcs(a.cell + i);
     s.frac = __ldcs(a.frac + i);
@@ -440,7 +492,7 @@ __device__ __forceinline__ void fetch_stream(const PushArgsMixed& a, int64_t i, 
   }
 }
 
-__device__ __forceinline__ void store_stream(const PushArgsMixed& a, int64_t i, const MixedState& s) {
+__device__ __forceinline__ void store_stream(const PushArgsMixed& a, uint32_t i, const MixedState& s) {
   __stcs(a.cell + i, s.cell);
   __stcs(a.frac + i, s.frac);
   __stcs(a.px + i, s.ux);
@@ -633,6 +685,11 @@ constexpr int kStashK = kDeferMin - 1;
 constexpr int kStashCap = 64;
 constexpr uint8_t kParity = 0x08;
 constexpr uint8_t kDeferMask = 0x70;
+// Deferred-k field value 1 (a k no sub-cycle is deferred with): the particle
+// belongs to the predicted queue, which pushes it every step until the next
+// refresh of the predictions; the stream leaves it alone.
+constexpr uint8_t kOwned = 0x10;
+static_assert(kDeferMin > 1, "deferred-k value 1 marks predicted-queue particles");
 
 __device__ __forceinline__ int deferred_k(uint8_t st) { return (st >> 4) & 7; }
 
@@ -662,6 +719,8 @@ struct Stash {
 
 // Push the first `cnt` (<= 32) stashed particles, one per lane, with 4^k
 // sub-steps each; then move entries [cnt, n) to the front.  Warp-collective.
+// Stash entry kp: k_prev in bits 0-2, bit 3 set for a predicted-queue particle
+// (which stays in that queue).
 template <int P, bool RING>
 __device__ __forceinline__ void stash_drain(const PushArgsMixed& a, const StepFields<P, RING>& F,
                                             Stash& S, int k, int& n, int cnt,
@@ -670,11 +729,13 @@ __device__ __forceinline__ void stash_drain(const PushArgsMixed& a, const StepFi
   if (lane < cnt) {
     MixedState s = {S.cell[lane], S.frac[lane], S.ux[lane], S.uy[lane], S.uz[lane]};
     const int32_t i = S.idx[lane];
-    const bool ok = subcycle_f32<P, RING, RING>(F, a.wtab, a.mask, a.dt, a.inv_dx, a.qm,
-                                                a.field_time, a.mono, k, S.kp[lane], 0.f, s);
+    const uint8_t kp = S.kp[lane];
+    const bool ok = subcycle_site<P, RING, RING>(F, a.wtab, a.mask, a.dt, a.inv_dx, a.qm,
+                                                 a.field_time, a.mono, k, kp & 7, 0.f, s);
     normalize(s);
     store_state(a, i, s);
-    a.status[i] = ok ? (uint8_t)(k | (a.parity_next ? kParity : 0)) : (uint8_t)(k | PIC_STATUS_LOST);
+    a.status[i] = ok ? (uint8_t)(k | (kp & 8 ? kOwned : 0) | (a.parity_next ? kParity : 0))
+                     : (uint8_t)(k | PIC_STATUS_LOST);
     if (!ok) atomicAdd(&sh[11], 1ull);
   }
   __syncwarp();
@@ -694,7 +755,8 @@ __device__ __forceinline__ void stash_drain(const PushArgsMixed& a, const StepFi
 }
 
 // Deferred item: particle i is in a step before this launch's (a long
-// sub-cycle, possibly partly done).  Finish it -- and, if it ran behind the
+// sub-cycle, possibly partly done), or -- a predicted particle -- starts the
+// long sub-cycle of this launch's step.  Finish it -- and, if it ran behind the
 // stream, every step up to the previous one, taking each step's criterion --
 // spending at most heavy_budget sub-steps of long sub-cycles; then take the
 // criterion of the current step: pushed at once if k < kDeferMin, else
@@ -729,9 +791,10 @@ __device__ __forceinline__ void heavy_particle(const PushArgsMixed& a, const Ste
     int j1 = m;
     if (k >= kDeferMin && m - j0 > budget) j1 = j0 + budget;
     bool ok;
-    if (si == a.step_cur - 1) {
-      ok = subcycle_f32<P, RING, RING>(Fp, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, a.field_time,
-                                       a.mono, k, k_prev, b0, s, j0, j1);
+    if (si >= a.step_cur - 1) {  // the previous or the current step: node tables
+      const StepFields<P, RING> Fs = si == a.step_cur ? Fc : Fp;
+      ok = subcycle_site<P, RING, RING>(Fs, a.wtab, a.mask, a.dt, a.inv_dx, a.qm, a.field_time,
+                                        a.mono, k, k_prev, b0, s, j0, j1);
     } else {
       if constexpr (RING) {
         const StepFields<P, true> Fs = ring_step_fields<P>(a, si);
@@ -755,6 +818,11 @@ __device__ __forceinline__ void heavy_particle(const PushArgsMixed& a, const Ste
       return;
     }
     normalize(s);
+    if (si == a.step_cur) {  // the current step's short sub-cycle is done
+      store_state(a, i, s);
+      a.status[i] = (uint8_t)(k | (a.parity_next ? kParity : 0));
+      return;
+    }
     if (si == a.step_cur - 1) {
       if (a.finalize) {
         store_state(a, i, s);
@@ -773,41 +841,34 @@ __device__ __forceinline__ void heavy_particle(const PushArgsMixed& a, const Ste
       const int kn = criterion_f32<P>(Fc.B, wcrit, jb, wb, a.mask, s, a.qm_abs, a.dt, a.psi_max,
                                       a.k_max, capped, b0);
       count_step(tc, sh, kn, capped);
-      if (kn < kDeferMin) {
-        const bool ok2 = subcycle_f32<P, RING, RING>(Fc, a.wtab, a.mask, a.dt, a.inv_dx, a.qm,
-                                                     a.field_time, a.mono, kn, k, b0, s);
-        normalize(s);
-        store_state(a, i, s);
-        a.status[i] = ok2 ? (uint8_t)(kn | (a.parity_next ? kParity : 0))
-                          : (uint8_t)(kn | PIC_STATUS_LOST);
-        if (!ok2) atomicAdd(&sh[11], 1ull);
-      } else {
+      if (kn >= kDeferMin) {
         store_state(a, i, s);
         defer_mark(a, i, k, kn, a.step_cur);
         defer_key = kn;
+        return;
       }
-      return;
+      // a short sub-cycle of the current step: the next pass of the loop
+      k_prev = k;
+      k = kn;
+      si = a.step_cur;
+      j0 = 0;
+      continue;
     }
     // behind the stream: the next step's criterion, then its sub-cycle
     if constexpr (RING) {
       si += 1;
-      const StepFields<P, true> Fs = si == a.step_cur - 1 ? StepFields<P, true>{} : ring_step_fields<P>(a, si);
-      const int32_t lo = si == a.step_cur - 1 ? Fp.lo : Fs.lo;
-      const int32_t hi = si == a.step_cur - 1 ? Fp.hi : Fs.hi;
+      const StepFields<P, true> Fs = si == a.step_cur - 1 ? Fp : ring_step_fields<P>(a, si);
       int32_t je, jb;
       float we, wb;
-      if (!tent_coords(s.cell, s.frac, lo, hi, je, we, jb, wb)) {
+      if (!tent_coords(s.cell, s.frac, Fs.lo, Fs.hi, je, we, jb, wb)) {
         store_state(a, i, s);
         a.status[i] = (uint8_t)(k | PIC_STATUS_LOST);
         atomicAdd(&sh[11], 1ull);
         return;
       }
       bool capped;
-      const int kn = si == a.step_cur - 1
-                         ? criterion_f32<P>(Fp.B, wcrit, jb, wb, a.mask, s, a.qm_abs, a.dt,
-                                            a.psi_max, a.k_max, capped, b0)
-                         : criterion_f32<P>(Fs.B, wcrit, jb, wb, a.mask, s, a.qm_abs, a.dt,
-                                            a.psi_max, a.k_max, capped, b0);
+      const int kn = criterion_f32<P>(Fs.B, wcrit, jb, wb, a.mask, s, a.qm_abs, a.dt, a.psi_max,
+                                      a.k_max, capped, b0);
       count_step(tc, sh, kn, capped);
       k_prev = k;
       k = kn;
@@ -822,18 +883,27 @@ __device__ __forceinline__ void heavy_particle(const PushArgsMixed& a, const Ste
   }
 }
 
-// Predicted item: particle i was binned before the launch as likely to take
-// k_pred; take its exact criterion.  k = 0 or k = k_pred: pushed at once.
-// Otherwise it goes where the stream would send it: k < kDeferMin to the
-// caller's stash (sk, with its state s and k_prev kp), else deferred (key).
+// Predicted item: particle i was binned at the last refresh of the
+// predictions as likely to take k_pred.  Skipped unless it still belongs to
+// the predicted queue (a particle deferred since then is the deferred items'
+// and then the stream's).  Takes its exact criterion: k = 0 is pushed at once;
+// k < kDeferMin goes to the caller's stash (sk, with its state s and stash
+// byte kp) and stays in the queue; a long sub-cycle leaves the queue and, with
+// resumable sub-cycles (run_heavy), starts at once in the caller's deferred-
+// particle code, at most heavy_budget sub-steps in this launch -- so a warp of
+// right predictions runs dense from the start of the launch -- else it is
+// deferred to the next launch (key), as the stream would.
 template <int P, bool RING>
 __device__ __forceinline__ void predicted_particle(const PushArgsMixed& a, const StepFields<P, RING>& Fc,
                                                    const float* wcrit, int64_t i, int k_pred,
                                                    ThreadCounters& tc, unsigned long long* sh,
-                                                   int& key, int& sk, MixedState& s, uint8_t& kp) {
+                                                   int& key, int& sk, MixedState& s, uint8_t& kp,
+                                                   bool& run_heavy) {
+  (void)k_pred;
   const uint8_t st = a.status[i];
+  if ((st & (PIC_STATUS_LOST | kDeferMask)) != kOwned) return;
   const int k_prev = st & 7;
-  kp = (uint8_t)k_prev;
+  kp = (uint8_t)(k_prev | 8);
   s = load_state(a, i);
   int32_t je, jb;
   float we, wb;
@@ -847,18 +917,21 @@ __device__ __forceinline__ void predicted_particle(const PushArgsMixed& a, const
   const int k = criterion_f32<P>(Fc.B, wcrit, jb, wb, a.mask, s, a.qm_abs, a.dt, a.psi_max,
                                  a.k_max, capped, b0);
   count_step(tc, sh, k, capped);
-  if (k == 0 || k == k_pred) {
-    const bool ok = subcycle_f32<P, RING, RING>(Fc, a.wtab, a.mask, a.dt, a.inv_dx, a.qm,
-                                                a.field_time, a.mono, k, k_prev, b0, s);
+  if (k == 0) {
+    const bool ok = subcycle_site<P, RING, RING>(Fc, a.wtab, a.mask, a.dt, a.inv_dx, a.qm,
+                                                 a.field_time, a.mono, 0, k_prev, b0, s);
     normalize(s);
     store_state(a, i, s);
-    a.status[i] = ok ? (uint8_t)(k | (a.parity_next ? kParity : 0)) : (uint8_t)(k | PIC_STATUS_LOST);
+    a.status[i] = ok ? (uint8_t)(kOwned | (a.parity_next ? kParity : 0)) : (uint8_t)PIC_STATUS_LOST;
     if (!ok) atomicAdd(&sh[11], 1ull);
   } else if (k < kDeferMin) {
     sk = k;
   } else {
-    defer_mark(a, i, k_prev, k, a.step_cur);
-    key = k;
+    defer_mark(a, i, k_prev, k, a.step_cur);  // in this step, none of its sub-steps done
+    if (RING && a.lag_step)
+      run_heavy = true;
+    else
+      key = k;
   }
 }
 

@@ -107,6 +107,10 @@ __global__ void halfstep_kernel(PushArgsMixed a, int64_t W, float* outE, float* 
     }
     outE[c] = fe;
     outB[c] = fb;
+    if (c == 0) {  // padding node W: the circular successor of node W - 1
+      outE[W] = fe;
+      outB[W] = fb;
+    }
     if (coef) {
       float e0[P + 1], e1[P + 1], b0[P + 1], b1[P + 1];
       to_monomial<P>(F.E, (int32_t)c, (int32_t)c, a.mono[0], e0, e1);
@@ -136,10 +140,12 @@ cudaError_t launch_halfstep(const PushArgsMixed& a, int order, int64_t W, float*
   return cudaGetLastError();
 }
 
-// Tent interpolation of a half-step field between nodes j, j+1.
+// Tent interpolation of a half-step field between nodes j, j+1.  The array
+// holds W + 1 nodes, node W repeating node 0, so the pair never wraps.
 __device__ __forceinline__ float half_lerp(const float* f, int32_t j, float w, int32_t mask) {
-  const float f0 = __ldg(f + (j & mask));
-  const float f1 = __ldg(f + ((j + 1) & mask));
+  const float* q = f + (j & mask);
+  const float f0 = __ldg(q);
+  const float f1 = __ldg(q + 1);
   return __fmaf_rn(w, __fsub_rn(f1, f0), f0);
 }
 
@@ -204,12 +210,13 @@ __global__ void __launch_bounds__(256) push_mixed_plain_kernel(PushArgsMixed a) 
 //     Each finishes that step, then takes its criterion for this one (pushed at
 //     once unless k >= kDeferMin again).  Being first, the longest serial
 //     chains start as the launch starts and run beside the stream below.
-//  2. predicted items (predicted schedule only): particles binned before the
-//     launch by the predictor's k (k >= kDeferMin), largest k first.  Each
-//     takes its exact criterion; k = 0 and k = the predicted k are pushed at
-//     once (so a warp of right predictions is dense), any other k goes where
-//     the stream would send it (stash or deferral), so a wrong prediction
-//     costs one idle lane.
+//  2. predicted items (predicted schedule only): particles binned at the last
+//     refresh of the predictions by the predictor's k (k >= kDeferMin),
+//     largest k first; the queue is kept, and its marked particles pushed by
+//     every launch, until the next refresh.  Each takes its exact criterion;
+//     k = 0 and k = the predicted k are pushed at once (so a warp of right
+//     predictions is dense), k = 1, 2 go to the stash and stay in the queue,
+//     a deferred k leaves it, so a wrong prediction costs one idle lane.
 //  3. stream chunks of kChunk particles, staged into shared memory tile by
 //     tile with bulk copies (one tile in flight while another is pushed),
 //     one particle per lane.  k = 0: pushed at once (the
@@ -222,9 +229,12 @@ __global__ void __launch_bounds__(256) push_mixed_plain_kernel(PushArgsMixed a) 
 // (the stream of step j takes particles whose parity equals j & 1 and flips
 // it), bits 4-6 = deferred k (0 = none), bit 7 = lost.
 
-// Before a predicted-schedule launch: particles the stream would take this
-// step and whose predicted k is >= min_k go into the queue of that k, and their
-// parity bit is flipped so the stream leaves them to the predicted items.
+// At a refresh of the predictions, before the step's launch: the predicted
+// queue is rebuilt.  Every particle of the old queue leaves it (its mark is
+// cleared); every particle the stream would take this step and whose predicted
+// k is >= min_k joins the queue of that k and is marked (deferred-k field 1),
+// so the streams leave it to the predicted items until the next refresh.
+// pred_count must be zero on entry.
 __global__ void bin_predicted_kernel(const uint8_t* pred, uint8_t* status, int64_t n,
                                      int parity_cur, int min_k, int32_t* pred_queue,
                                      int32_t* pred_count, int64_t qcap) {
@@ -255,44 +265,45 @@ __global__ void bin_predicted_kernel(const uint8_t* pred, uint8_t* status, int64
     }
     int keys[16];
     bool any = false;
+    uint32_t nw[4] = {sw[0], sw[1], sw[2], sw[3]};  // the bytes after this pass
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      const uint8_t st = (uint8_t)(sw[q >> 2] >> (8 * (q & 3)));
-      const int kp = (int)((pw[q >> 2] >> (8 * (q & 3))) & 0xffu);
-      keys[q] = (!(st & PIC_STATUS_LOST) && !(st & kDeferMask) && ((st & kParity) == want) &&
-                 kp >= min_k && kp <= 7)
+      const int sh8 = 8 * (q & 3);
+      uint8_t st = (uint8_t)(sw[q >> 2] >> sh8);
+      const int kp = (int)((pw[q >> 2] >> sh8) & 0xffu);
+      if ((st & kDeferMask) == kOwned) st = (uint8_t)(st & ~kDeferMask);  // leaves the old queue
+      keys[q] = ((st & (PIC_STATUS_LOST | kDeferMask | kParity)) == want && kp >= min_k && kp <= 7)
                     ? kp
                     : 0;
+      if (keys[q]) st = (uint8_t)(st | kOwned);
+      nw[q >> 2] = (nw[q >> 2] & ~(0xffu << sh8)) | ((uint32_t)st << sh8);
       any |= keys[q] != 0;
     }
-    if (!__syncthreads_or(any)) continue;
-    if (threadIdx.x < 8) blk_cnt[threadIdx.x] = 0;
-    __syncthreads();
-    int off[16];
+    if (__syncthreads_or(any)) {
+      if (threadIdx.x < 8) blk_cnt[threadIdx.x] = 0;
+      __syncthreads();
+      int off[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) off[q] = keys[q] ? atomicAdd(&blk_cnt[keys[q]], 1) : 0;
-    __syncthreads();
-    if (threadIdx.x > 0 && threadIdx.x < 8 && blk_cnt[threadIdx.x] > 0)
-      blk_base[threadIdx.x] = atomicAdd(&pred_count[threadIdx.x], blk_cnt[threadIdx.x]);
-    __syncthreads();
-    uint32_t flip[4] = {0u, 0u, 0u, 0u};
+      for (int q = 0; q < 16; ++q) off[q] = keys[q] ? atomicAdd(&blk_cnt[keys[q]], 1) : 0;
+      __syncthreads();
+      if (threadIdx.x > 0 && threadIdx.x < 8 && blk_cnt[threadIdx.x] > 0)
+        blk_base[threadIdx.x] = atomicAdd(&pred_count[threadIdx.x], blk_cnt[threadIdx.x]);
+      __syncthreads();
 #pragma unroll
-    for (int q = 0; q < 16; ++q)
-      if (keys[q]) {
-        pred_queue[(int64_t)(keys[q] - 1) * qcap + blk_base[keys[q]] + off[q]] = (int32_t)(i0 + q);
-        flip[q >> 2] |= (uint32_t)kParity << (8 * (q & 3));
-      }
-    if (flip[0] | flip[1] | flip[2] | flip[3]) {
+      for (int q = 0; q < 16; ++q)
+        if (keys[q])
+          pred_queue[(int64_t)(keys[q] - 1) * qcap + blk_base[keys[q]] + off[q]] = (int32_t)(i0 + q);
+      __syncthreads();  // blk_cnt / blk_base are reused by the next pass
+    }
+    if ((nw[0] ^ sw[0]) | (nw[1] ^ sw[1]) | (nw[2] ^ sw[2]) | (nw[3] ^ sw[3])) {
       if (i0 + 16 <= n) {
-        reinterpret_cast<uint4*>(status)[v] =
-            make_uint4(sw[0] ^ flip[0], sw[1] ^ flip[1], sw[2] ^ flip[2], sw[3] ^ flip[3]);
+        reinterpret_cast<uint4*>(status)[v] = make_uint4(nw[0], nw[1], nw[2], nw[3]);
       } else {
         for (int q = 0; q < 16 && i0 + q < n; ++q)
-          if ((flip[q >> 2] >> (8 * (q & 3))) & 0xffu)
-            status[i0 + q] = (uint8_t)((sw[q >> 2] ^ flip[q >> 2]) >> (8 * (q & 3)));
+          if (((nw[q >> 2] ^ sw[q >> 2]) >> (8 * (q & 3))) & 0xffu)
+            status[i0 + q] = (uint8_t)(nw[q >> 2] >> (8 * (q & 3)));
       }
     }
-    __syncthreads();  // blk_cnt / blk_base are reused by the next pass
   }
 }
 
@@ -374,9 +385,37 @@ __global__ void __launch_bounds__(kThreads, PIC_BINNED_MIN_BLOCKS) push_binned_k
   const int64_t n_chunks = a.finalize ? 0 : (a.n + kChunk - 1) / kChunk;
   const int64_t n_items = n_pred_end + n_chunks;
 
+  // the stashes' fill counts, read and written at a run-time stash index
+  auto stash_count = [&](int q) {
+    int v = 0;
+#pragma unroll
+    for (int r = 0; r < kStashK; ++r)
+      if (r == q) v = stash_n[r];
+    return v;
+  };
+  auto stash_set = [&](int q, int v) {
+#pragma unroll
+    for (int r = 0; r < kStashK; ++r)
+      if (r == q) stash_n[r] = v;
+  };
+  // push 32 particles of every stash that holds 32 or more (all = true: every
+  // parked particle); one call site of the sub-cycle per call site of this
+  auto drain = [&](bool all) {
+#pragma unroll 1
+    for (int q = 0; q < kStashK; ++q) {
+      int n = stash_count(q);
+      const int cnt = all ? n : (n >= 32 ? 32 : 0);
+      if (cnt > 0) {
+        stash_drain<P, RING>(a, F, my_stash[q], q + 1, n, cnt, sh);
+        stash_set(q, n);
+      }
+    }
+  };
+
   // park k = 1, 2 in the warp's stashes; push a stash when it holds 32
   // (warp-collective; sk = 0: nothing to park)
-  auto park = [&](int sk, int32_t i, const MixedState& s, uint8_t k_prev) {
+  auto park = [&](int sk, int32_t i, const MixedState& s, uint8_t kp) {
+    bool full = false;
 #pragma unroll
     for (int q = 0; q < kStashK; ++q) {
       const unsigned m = __ballot_sync(0xffffffffu, sk == q + 1);
@@ -390,25 +429,27 @@ __global__ void __launch_bounds__(kThreads, PIC_BINNED_MIN_BLOCKS) push_binned_k
         S.ux[pos] = s.ux;
         S.uy[pos] = s.uy;
         S.uz[pos] = s.uz;
-        S.kp[pos] = k_prev;
+        S.kp[pos] = kp;
       }
       stash_n[q] += __popc(m);
-      __syncwarp();
-      if (stash_n[q] >= 32) stash_drain<P, RING>(a, F, S, q + 1, stash_n[q], 32, sh);
+      full |= stash_n[q] >= 32;
     }
+    __syncwarp();
+    if (full) drain(false);
   };
 
   // one stream particle: criterion, then push (k = 0), park (k = 1, 2) or
-  // defer (k >= kDeferMin).  Warp-collective.
-  auto stream_one = [&](int64_t i, uint8_t st, MixedState s) {
-    const bool mine = i < a.n && !(st & PIC_STATUS_LOST) && !(st & kDeferMask) &&
-                      ((st & kParity) == want);
-    int key = 0, sk = 0;
+  // defer (k >= kDeferMin).  Warp-collective.  A round in which every lane's
+  // particle takes k = 0 (or is not the stream's) -- nearly all of them --
+  // skips the cap test, the queues and the stashes.
+  constexpr uint8_t kStreamMask = PIC_STATUS_LOST | kDeferMask | kParity;
+  auto stream_one = [&](uint32_t i, uint8_t st, MixedState s) {
+    const bool mine = (st & kStreamMask) == want;  // lost (and so i >= n) excluded
+    int32_t je = 0, jb = 0;
+    float we = 0.f, wb = 0.f, b0 = 0.f, ey = 0.f;
+    bool inwin = false, push = false;
     if (mine) {
-      int32_t je, jb;
-      float we, wb;
-      const bool inwin = tent_coords(s.cell, s.frac, F.lo, F.hi, je, we, jb, wb);
-      float b0, ey;
+      inwin = tent_coords(s.cell, s.frac, F.lo, F.hi, je, we, jb, wb);
       if (a.halfE) {
         b0 = half_lerp(a.halfB, jb, wb, a.mask);
         ey = half_lerp(a.halfE, je, we, a.mask);
@@ -416,6 +457,16 @@ __global__ void __launch_bounds__(kThreads, PIC_BINNED_MIN_BLOCKS) push_binned_k
         b0 = gather_f32<P>(F.B, wcrit, jb, wb, a.mask);
         ey = gather_f32<P>(F.E, w0, je, we, a.mask);
       }
+      float a2, rhs;
+      psi_terms(b0, s, a.qm_abs, a.dt, a.psi_max, a2, rhs);
+      push = inwin && !(a2 > rhs);  // psi_to_k's k = 0 without a cap
+    }
+    const int k_prev = st & 7;
+    const bool fast = __all_sync(0xffffffffu, push || !mine);
+    int key = 0, sk = 0;
+    if (fast) {
+      tc.k0 += push ? 1u : 0u;
+    } else if (mine) {
       if (!inwin) {
         a.status[i] = (uint8_t)(st | PIC_STATUS_LOST);
         atomicAdd(&sh[11], 1ull);
@@ -423,24 +474,26 @@ __global__ void __launch_bounds__(kThreads, PIC_BINNED_MIN_BLOCKS) push_binned_k
         bool capped;
         const int k = psi_to_k(b0, s, a.qm_abs, a.dt, a.psi_max, a.k_max, capped);
         count_step(tc, sh, k, capped);
-        const int k_prev = st & 7;
-        if (k == 0) {
-          const float h_old = pow4_down(a.dt, k_prev);
-          const float hp = __fmul_rn(0.5f, __fadd_rn(h_old, a.dt));
-          boris_f32(ey, b0, hp, hx0, a.qm, s);
-          normalize(s);
-          store_stream(a, i, s);
-          a.status[i] = done;
-        } else if (k < kDeferMin) {
-          sk = k;
-        } else {
+        push = k == 0;
+        if (k >= kDeferMin) {
           defer_mark(a, i, k_prev, k, a.step_cur);
           key = k;
+        } else if (k > 0) {
+          sk = k;
         }
       }
     }
-    enqueue(a, key, (int32_t)i);
-    park(sk, (int32_t)i, s, (uint8_t)(st & 7));
+    if (push) {
+      const float hp = __fmul_rn(0.5f, __fadd_rn(pow4_down(a.dt, k_prev), a.dt));
+      boris_f32(ey, b0, hp, hx0, a.qm, s);
+      normalize(s);
+      store_stream(a, i, s);
+      a.status[i] = done;
+    }
+    if (!fast) {
+      enqueue(a, key, (int32_t)i);
+      park(sk, (int32_t)i, s, (uint8_t)k_prev);
+    }
   };
 
   auto claim = [&]() -> int64_t {
@@ -451,37 +504,37 @@ __global__ void __launch_bounds__(kThreads, PIC_BINNED_MIN_BLOCKS) push_binned_k
     return t;
   };
 
-  // deferred and predicted items first (they come first in the cursor order)
+  // deferred and predicted items first (they come first in the cursor order);
+  // one call site each of the deferred-particle code, enqueue and park
   int64_t t = claim();
   while (t < n_pred_end) {
+    int key = 0, sk = 0;
+    int32_t i = 0;
+    MixedState s = {0, 0.5f, 0.f, 0.f, 0.f};
+    uint8_t kp = 0;
+    bool heavy = false;
     if (t < n_heavy) {
       int k = 7;
       while (k > 1 && t >= heavy_end[k]) --k;
       const int64_t first = (k == 7 ? 0 : heavy_end[k + 1]);
       const int64_t e = (t - first) * 32 + lane;
-      int key = 0;
-      int32_t i = 0;
       if (e < a.qcount_in[k]) {
         i = a.queue_in[(int64_t)(k - 1) * a.qcap + e];
-        heavy_particle<P, RING>(a, Fp, F, wcrit, i, tc, sh, key);
+        heavy = true;
       }
-      enqueue(a, key, i);
     } else {
       int k = 7;
       while (k > 1 && t >= pred_end[k]) --k;
       const int64_t first = (k == 7 ? n_heavy : pred_end[k + 1]);
       const int64_t e = (t - first) * 32 + lane;
-      int key = 0, sk = 0;
-      int32_t i = 0;
-      MixedState s = {0, 0.5f, 0.f, 0.f, 0.f};
-      uint8_t kp = 0;
       if (e < a.pred_count[k]) {
         i = a.pred_queue[(int64_t)(k - 1) * a.qcap + e];
-        predicted_particle<P, RING>(a, F, wcrit, i, k, tc, sh, key, sk, s, kp);
+        predicted_particle<P, RING>(a, F, wcrit, i, k, tc, sh, key, sk, s, kp, heavy);
       }
-      enqueue(a, key, i);
-      park(sk, i, s, kp);
     }
+    if (heavy) heavy_particle<P, RING>(a, Fp, F, wcrit, i, tc, sh, key);
+    enqueue(a, key, i);
+    park(sk, i, s, kp);
     t = claim();
   }
 
@@ -544,20 +597,24 @@ __global__ void __launch_bounds__(kThreads, PIC_BINNED_MIN_BLOCKS) push_binned_k
             break;
           }
           phase ^= 1u << sidx;
-          const Tile& T = my_tiles[sidx];
+        }
+        // one call site of stream_one: staged tiles from shared memory, the
+        // rest (the array's tail, unaligned arrays) by plain loads
+        const bool staged = whole(tile);
+        const Tile& T = my_tiles[sidx];
 #pragma unroll 1
-          for (int r = 0; r < kTile / 32; ++r) {
-            const int j = r * 32 + lane;
-            stream_one(first + j, T.st[j], MixedState{T.cell[j], T.frac[j], T.px[j], T.py[j], T.pz[j]});
+        for (int r = 0; r < kTile / 32; ++r) {
+          const int j = r * 32 + lane;
+          const uint32_t i = (uint32_t)first + (uint32_t)j;
+          uint8_t st;
+          MixedState s;
+          if (staged) {
+            st = T.st[j];
+            s = MixedState{T.cell[j], T.frac[j], T.px[j], T.py[j], T.pz[j]};
+          } else {
+            fetch_stream(a, i, st, s);
           }
-        } else {
-#pragma unroll 1
-          for (int r = 0; r < kTile / 32; ++r) {
-            uint8_t st;
-            MixedState s;
-            fetch_stream(a, first + r * 32 + lane, st, s);
-            stream_one(first + r * 32 + lane, st, s);
-          }
+          stream_one(i, st, s);
         }
         __syncwarp();  // every lane is done with the stage before it is refilled
         q[sidx] = gen();
@@ -567,9 +624,7 @@ __global__ void __launch_bounds__(kThreads, PIC_BINNED_MIN_BLOCKS) push_binned_k
   }
 
   // push what is left in the stashes
-#pragma unroll
-  for (int q = 0; q < kStashK; ++q)
-    if (stash_n[q] > 0) stash_drain<P, RING>(a, F, my_stash[q], q + 1, stash_n[q], stash_n[q], sh);
+  drain(true);
   flush_counters(tc, sh, a.stats);
 
   // the last block to finish resets the cursor and the consumed queue counts
@@ -582,8 +637,6 @@ __global__ void __launch_bounds__(kThreads, PIC_BINNED_MIN_BLOCKS) push_binned_k
       *a.cursor = 0;
       *a.blocks_done = 0;
       for (int k = 0; k < 8; ++k) a.qcount_in[k] = 0;
-      if (a.pred_count)
-        for (int k = 0; k < 8; ++k) a.pred_count[k] = 0;
       __threadfence();
     }
   }
