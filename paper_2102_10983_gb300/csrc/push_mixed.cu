@@ -324,8 +324,12 @@ constexpr size_t kStashBytes = sizeof(Stash) * kWarps * kStashK;
 constexpr size_t kBinnedSmem = kStashBytes + sizeof(Tile) * kWarps * kStages;
 static_assert(kStashBytes % 128 == 0, "tiles start on a 128-byte boundary");
 
+// Two resident blocks (16 warps) per SM: up to 128 registers a thread, and
+// fewer warps contending for the instruction cache across the kernel's
+// stream, stash and deferred-particle code (measured faster than three blocks
+// at 80 registers).
 #ifndef PIC_BINNED_MIN_BLOCKS
-#define PIC_BINNED_MIN_BLOCKS 3
+#define PIC_BINNED_MIN_BLOCKS 2
 #endif
 
 template <int P, bool RING>
