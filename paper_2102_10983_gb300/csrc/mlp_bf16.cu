@@ -26,6 +26,10 @@ namespace pic {
 namespace {
 
 constexpr int kH = 64, kIn = 6, kOut = 8, kK1 = 16;
+// Row strides (BF16 elements) of the weight tiles in shared memory, padded so
+// that the eight rows a warp's B-fragment loads touch at once fall in distinct
+// banks (a 64-element row is 128 bytes: unpadded, those eight loads conflict).
+constexpr int kS1 = 24, kS2 = 72;
 
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -43,13 +47,14 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], 
 }
 
 // Weights as the kernels read them from shared memory (BF16):
-//   W1p [64][16] (cols 6..15 zero), W2 [64][64], W2T [64][64], W3 [8][64], W3T [64][8],
+//   W1p [64][16] (cols 6..15 zero), W2 [64][64], W2T [64][64], W3 [8][64] (rows at the
+//   padded strides kS1, kS2), W3T [64][8],
 // and the FP32 biases.
 struct SmemW {
-  __nv_bfloat16 W1p[kH * kK1];
-  __nv_bfloat16 W2[kH * kH];
-  __nv_bfloat16 W2T[kH * kH];
-  __nv_bfloat16 W3[kOut * kH];
+  __nv_bfloat16 W1p[kH * kS1];
+  __nv_bfloat16 W2[kH * kS2];
+  __nv_bfloat16 W2T[kH * kS2];
+  __nv_bfloat16 W3[kOut * kS2];
   __nv_bfloat16 W3T[kH * kOut];
   float b1[kH], b2[kH], b3[kOut];
 };
@@ -64,16 +69,16 @@ __device__ void load_weights(SmemW& s, const float* P) {
   const float* b3 = W3 + kOut * kH;
   for (int e = threadIdx.x; e < kH * kK1; e += blockDim.x) {
     const int o = e / kK1, i = e % kK1;
-    s.W1p[e] = __float2bfloat16_rn(i < kIn ? W1[o * kIn + i] : 0.0f);
+    s.W1p[o * kS1 + i] = __float2bfloat16_rn(i < kIn ? W1[o * kIn + i] : 0.0f);
   }
   for (int e = threadIdx.x; e < kH * kH; e += blockDim.x) {
     const int o = e / kH, i = e % kH;
-    s.W2[e] = __float2bfloat16_rn(W2[e]);
-    s.W2T[i * kH + o] = __float2bfloat16_rn(W2[e]);
+    s.W2[o * kS2 + i] = __float2bfloat16_rn(W2[e]);
+    s.W2T[i * kS2 + o] = __float2bfloat16_rn(W2[e]);
   }
   for (int e = threadIdx.x; e < kOut * kH; e += blockDim.x) {
     const int o = e / kH, i = e % kH;
-    s.W3[e] = __float2bfloat16_rn(W3[e]);
+    s.W3[o * kS2 + i] = __float2bfloat16_rn(W3[e]);
     s.W3T[i * kOut + o] = __float2bfloat16_rn(W3[e]);
   }
   for (int e = threadIdx.x; e < kH; e += blockDim.x) {
@@ -100,7 +105,7 @@ __device__ __forceinline__ void forward_tile(const SmemW& s, const uint32_t (&a1
   for (int nt = 0; nt < 8; ++nt) {
     const float bl = s.b1[8 * nt + 2 * t], bh = s.b1[8 * nt + 2 * t + 1];
     f.acc1[nt][0] = bl; f.acc1[nt][1] = bh; f.acc1[nt][2] = bl; f.acc1[nt][3] = bh;
-    const __nv_bfloat16* w = s.W1p + (8 * nt + g) * kK1;
+    const __nv_bfloat16* w = s.W1p + (8 * nt + g) * kS1;
     mma16816(f.acc1[nt], a1, ld32(w + 2 * t), ld32(w + 2 * t + 8));
   }
   uint32_t a2[4][4];
@@ -115,7 +120,7 @@ __device__ __forceinline__ void forward_tile(const SmemW& s, const uint32_t (&a1
   for (int nt = 0; nt < 8; ++nt) {
     const float bl = s.b2[8 * nt + 2 * t], bh = s.b2[8 * nt + 2 * t + 1];
     f.acc2[nt][0] = bl; f.acc2[nt][1] = bh; f.acc2[nt][2] = bl; f.acc2[nt][3] = bh;
-    const __nv_bfloat16* w = s.W2 + (8 * nt + g) * kH;
+    const __nv_bfloat16* w = s.W2 + (8 * nt + g) * kS2;
 #pragma unroll
     for (int kc = 0; kc < 4; ++kc)
       mma16816(f.acc2[nt], a2[kc], ld32(w + 16 * kc + 2 * t), ld32(w + 16 * kc + 2 * t + 8));
@@ -130,7 +135,7 @@ __device__ __forceinline__ void forward_tile(const SmemW& s, const uint32_t (&a1
   }
   const float bl = s.b3[2 * t], bh = s.b3[2 * t + 1];
   f.z[0] = bl; f.z[1] = bh; f.z[2] = bl; f.z[3] = bh;
-  const __nv_bfloat16* w = s.W3 + g * kH;
+  const __nv_bfloat16* w = s.W3 + g * kS2;
 #pragma unroll
   for (int kc = 0; kc < 4; ++kc)
     mma16816(f.z, a3[kc], ld32(w + 16 * kc + 2 * t), ld32(w + 16 * kc + 2 * t + 8));
@@ -213,7 +218,7 @@ __device__ __forceinline__ void infer_tiles2(const SmemW& s, const uint32_t (&x0
   for (int nt = 0; nt < 8; ++nt) {
     const float bl = s.b1[8 * nt + 2 * t], bh = s.b1[8 * nt + 2 * t + 1];
     float c0[4] = {bl, bh, bl, bh}, c1[4] = {bl, bh, bl, bh};
-    const __nv_bfloat16* w = s.W1p + (8 * nt + g) * kK1;
+    const __nv_bfloat16* w = s.W1p + (8 * nt + g) * kS1;
     const uint32_t b0 = ld32(w + 2 * t), b1 = ld32(w + 2 * t + 8);
     mma16816(c0, x0, b0, b1);
     mma16816(c1, x1, b0, b1);
@@ -228,7 +233,7 @@ __device__ __forceinline__ void infer_tiles2(const SmemW& s, const uint32_t (&x0
   for (int nt = 0; nt < 8; ++nt) {
     const float bl = s.b2[8 * nt + 2 * t], bh = s.b2[8 * nt + 2 * t + 1];
     float c0[4] = {bl, bh, bl, bh}, c1[4] = {bl, bh, bl, bh};
-    const __nv_bfloat16* w = s.W2 + (8 * nt + g) * kH;
+    const __nv_bfloat16* w = s.W2 + (8 * nt + g) * kS2;
 #pragma unroll
     for (int kc = 0; kc < 4; ++kc) {
       const uint32_t b0 = ld32(w + 16 * kc + 2 * t), b1 = ld32(w + 16 * kc + 2 * t + 8);
@@ -244,7 +249,7 @@ __device__ __forceinline__ void infer_tiles2(const SmemW& s, const uint32_t (&x0
   const float bl = s.b3[2 * t], bh = s.b3[2 * t + 1];
   z0[0] = bl; z0[1] = bh; z0[2] = bl; z0[3] = bh;
   z1[0] = bl; z1[1] = bh; z1[2] = bl; z1[3] = bh;
-  const __nv_bfloat16* w = s.W3 + g * kH;
+  const __nv_bfloat16* w = s.W3 + g * kS2;
 #pragma unroll
   for (int kc = 0; kc < 4; ++kc) {
     const uint32_t b0 = ld32(w + 16 * kc + 2 * t), b1 = ld32(w + 16 * kc + 2 * t + 8);
@@ -262,8 +267,10 @@ __device__ __forceinline__ void infer_tiles2(const SmemW& s, const uint32_t (&x0
 // The same predictions as the features kernel followed by mlp_infer_kernel,
 // without the 24 bytes per particle of features going through HBM.
 template <int P>
+// Four resident blocks per SM (at most 128 registers a thread): measured
+// faster than the register-unbounded build at three.
 #ifndef PIC_PREDICT_MIN_BLOCKS
-#define PIC_PREDICT_MIN_BLOCKS 1
+#define PIC_PREDICT_MIN_BLOCKS 4
 #endif
 __global__ void __launch_bounds__(128, PIC_PREDICT_MIN_BLOCKS) predict_kernel(PushArgsMixed a, const float* Pm,
                                                       uint8_t* pred) {
@@ -413,7 +420,7 @@ __global__ void __launch_bounds__(128) mlp_grad_kernel(const float* P, const flo
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
       dh1[nt][0] = dh1[nt][1] = dh1[nt][2] = dh1[nt][3] = 0.f;
-      const __nv_bfloat16* w = s.W2T + (8 * nt + g) * kH;
+      const __nv_bfloat16* w = s.W2T + (8 * nt + g) * kS2;
 #pragma unroll
       for (int kc = 0; kc < 4; ++kc)
         mma16816(dh1[nt], ada2[kc], ld32(w + 16 * kc + 2 * t), ld32(w + 16 * kc + 2 * t + 8));
