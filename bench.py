@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--acc-particles", type=int, default=524288)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--predict-every", type=int, default=16)
+    ap.add_argument("--predict-every", type=int, default=64)
     ap.add_argument("--batched-steps", type=int, default=200)
     ap.add_argument("--batched-ensembles", type=int, default=512)
     ap.add_argument("--cpu-sample", type=int, default=16384)

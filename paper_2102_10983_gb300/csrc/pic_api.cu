@@ -694,7 +694,7 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
                                      c->stream);
             ++launches;
             if (e == cudaSuccess)
-              e = launch_bin_predicted(c->pred, c->status, c->n, a.parity_cur, kDeferMin,
+              e = launch_bin_predicted(c->pred, c->status, c->n, a.parity_cur, kPredMinK,
                                        c->pred_queue, c->qcount + 32, c->capacity, c->stream);
             ++launches;
           }

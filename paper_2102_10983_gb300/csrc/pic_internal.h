@@ -15,6 +15,14 @@ constexpr int kMaxK = 7;
 // first work items (shorter ones are compacted inside the warp); also the
 // smallest predicted k the predicted schedule bins before a launch.
 constexpr int kDeferMin = 3;
+// Predicted schedule: smallest predicted k that puts a particle in the
+// predicted queue.  The long sub-cycles only: binning the short ones too (1)
+// took them out of the stream's stashes but measured slower, the network
+// over-predicting k = 2 and a predicted item costing more than a stream slot.
+#ifndef PIC_PRED_MIN_K
+#define PIC_PRED_MIN_K 3
+#endif
+constexpr int kPredMinK = PIC_PRED_MIN_K;
 
 // Device counters of one context (accumulated by every push launch).
 struct DevStats {

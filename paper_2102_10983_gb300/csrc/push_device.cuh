@@ -886,9 +886,11 @@ __device__ __forceinline__ void heavy_particle(const PushArgsMixed& a, const Ste
 // Predicted item: particle i was binned at the last refresh of the
 // predictions as likely to take k_pred.  Skipped unless it still belongs to
 // the predicted queue (a particle deferred since then is the deferred items'
-// and then the stream's).  Takes its exact criterion: k = 0 is pushed at once;
-// k < kDeferMin goes to the caller's stash (sk, with its state s and stash
-// byte kp) and stays in the queue; a long sub-cycle leaves the queue and, with
+// and then the stream's).  Takes its exact criterion: k = 0, and a short k
+// equal to the predicted one, are pushed at once (a warp of right predictions
+// runs dense); another short k goes to the caller's stash (sk, with its state
+// s and stash byte kp); both stay in the queue.  A long sub-cycle leaves the
+// queue and, with
 // resumable sub-cycles (run_heavy), starts at once in the caller's deferred-
 // particle code, at most heavy_budget sub-steps in this launch -- so a warp of
 // right predictions runs dense from the start of the launch -- else it is
@@ -899,7 +901,6 @@ __device__ __forceinline__ void predicted_particle(const PushArgsMixed& a, const
                                                    ThreadCounters& tc, unsigned long long* sh,
                                                    int& key, int& sk, MixedState& s, uint8_t& kp,
                                                    bool& run_heavy) {
-  (void)k_pred;
   const uint8_t st = a.status[i];
   if ((st & (PIC_STATUS_LOST | kDeferMask)) != kOwned) return;
   const int k_prev = st & 7;
@@ -917,12 +918,13 @@ __device__ __forceinline__ void predicted_particle(const PushArgsMixed& a, const
   const int k = criterion_f32<P>(Fc.B, wcrit, jb, wb, a.mask, s, a.qm_abs, a.dt, a.psi_max,
                                  a.k_max, capped, b0);
   count_step(tc, sh, k, capped);
-  if (k == 0) {
+  if (k == 0 || (k == k_pred && k < kDeferMin)) {
     const bool ok = subcycle_site<P, RING, RING>(Fc, a.wtab, a.mask, a.dt, a.inv_dx, a.qm,
-                                                 a.field_time, a.mono, 0, k_prev, b0, s);
+                                                 a.field_time, a.mono, k, k_prev, b0, s);
     normalize(s);
     store_state(a, i, s);
-    a.status[i] = ok ? (uint8_t)(kOwned | (a.parity_next ? kParity : 0)) : (uint8_t)PIC_STATUS_LOST;
+    a.status[i] = ok ? (uint8_t)(k | kOwned | (a.parity_next ? kParity : 0))
+                     : (uint8_t)(k | PIC_STATUS_LOST);
     if (!ok) atomicAdd(&sh[11], 1ull);
   } else if (k < kDeferMin) {
     sk = k;

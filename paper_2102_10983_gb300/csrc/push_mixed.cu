@@ -211,12 +211,13 @@ __global__ void __launch_bounds__(256) push_mixed_plain_kernel(PushArgsMixed a) 
 //     once unless k >= kDeferMin again).  Being first, the longest serial
 //     chains start as the launch starts and run beside the stream below.
 //  2. predicted items (predicted schedule only): particles binned at the last
-//     refresh of the predictions by the predictor's k (k >= kDeferMin),
+//     refresh of the predictions by the predictor's k (k >= kPredMinK),
 //     largest k first; the queue is kept, and its marked particles pushed by
 //     every launch, until the next refresh.  Each takes its exact criterion;
-//     k = 0 and k = the predicted k are pushed at once (so a warp of right
-//     predictions is dense), k = 1, 2 go to the stash and stay in the queue,
-//     a deferred k leaves it, so a wrong prediction costs one idle lane.
+//     k = 0 and a short k equal to the predicted one are pushed at once (so a
+//     warp of right predictions is dense), another short k goes to the stash,
+//     both staying in the queue; a long sub-cycle starts at once (resumable)
+//     and leaves the queue; a wrong prediction costs one idle lane.
 //  3. stream chunks of kChunk particles, staged into shared memory tile by
 //     tile with bulk copies (one tile in flight while another is pushed),
 //     one particle per lane.  k = 0: pushed at once (the
