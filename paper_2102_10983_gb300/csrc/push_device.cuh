@@ -710,12 +710,21 @@ __device__ __forceinline__ void enqueue(const PushArgsMixed& a, int key, int32_t
 }
 
 // A warp's stash of particles waiting for a short sub-cycle of one k.
+#ifdef PIC_STASH_INDEX_ONLY
+// (index only: the drain reads the state back from global memory, leaving
+// more of the SM's on-chip memory to the L1 cache)
+struct Stash {
+  int32_t idx[kStashCap];
+  uint8_t kp[kStashCap];
+};
+#else
 struct Stash {
   int32_t idx[kStashCap];
   int32_t cell[kStashCap];
   float frac[kStashCap], ux[kStashCap], uy[kStashCap], uz[kStashCap];
   uint8_t kp[kStashCap];
 };
+#endif
 
 // Push the first `cnt` (<= 32) stashed particles, one per lane, with 4^k
 // sub-steps each; then move entries [cnt, n) to the front.  Warp-collective.
@@ -727,8 +736,12 @@ __device__ __forceinline__ void stash_drain(const PushArgsMixed& a, const StepFi
                                             unsigned long long* sh) {
   const int lane = threadIdx.x & 31;
   if (lane < cnt) {
-    MixedState s = {S.cell[lane], S.frac[lane], S.ux[lane], S.uy[lane], S.uz[lane]};
     const int32_t i = S.idx[lane];
+#ifdef PIC_STASH_INDEX_ONLY
+    MixedState s = load_state(a, i);
+#else
+    MixedState s = {S.cell[lane], S.frac[lane], S.ux[lane], S.uy[lane], S.uz[lane]};
+#endif
     const uint8_t kp = S.kp[lane];
     const bool ok = subcycle_site<P, RING, RING>(F, a.wtab, a.mask, a.dt, a.inv_dx, a.qm,
                                                  a.field_time, a.mono, k, kp & 7, 0.f, s);
@@ -743,11 +756,13 @@ __device__ __forceinline__ void stash_drain(const PushArgsMixed& a, const StepFi
   if (lane < rest) {
     const int q = cnt + lane;
     S.idx[lane] = S.idx[q];
+#ifndef PIC_STASH_INDEX_ONLY
     S.cell[lane] = S.cell[q];
     S.frac[lane] = S.frac[q];
     S.ux[lane] = S.ux[q];
     S.uy[lane] = S.uy[q];
     S.uz[lane] = S.uz[q];
+#endif
     S.kp[lane] = S.kp[q];
   }
   __syncwarp();

@@ -429,11 +429,13 @@ __global__ void __launch_bounds__(kThreads, PIC_BINNED_MIN_BLOCKS) push_binned_k
       if (sk == q + 1) {
         const int pos = stash_n[q] + __popc(m & ((1u << lane) - 1u));
         S.idx[pos] = i;
+#ifndef PIC_STASH_INDEX_ONLY
         S.cell[pos] = s.cell;
         S.frac[pos] = s.frac;
         S.ux[pos] = s.ux;
         S.uy[pos] = s.uy;
         S.uz[pos] = s.uz;
+#endif
         S.kp[pos] = kp;
       }
       stash_n[q] += __popc(m);
@@ -573,58 +575,60 @@ __global__ void __launch_bounds__(kThreads, PIC_BINNED_MIN_BLOCKS) push_binned_k
       if (tile >= 0 && whole(tile) && lane == 0)
         tile_issue(a, my_tiles + sidx, my_bars + sidx, tile * kTile, policy);
     };
+    // q[o]: the tile staged in stage (stage + o) % kStages, o = 0 the next one
+    // pushed.  The loop body -- the whole stream code -- exists once: the
+    // stages rotate through registers instead of an unrolled loop per stage.
     int64_t q[kStages];
 #pragma unroll
     for (int sidx = 0; sidx < kStages; ++sidx) {
       q[sidx] = gen();
       issue(sidx, q[sidx]);
     }
-    bool stop = false;
-    while (!stop) {
+    int stage = 0;
+#pragma unroll 1
+    for (;;) {
+      const int64_t tile = q[0];
+      if (tile < 0) break;
+      const int64_t first = tile * kTile;
+      const bool staged = whole(tile);
+      if (staged) {
+        if (!mbar_wait(my_bars + stage, (phase >> stage) & 1u)) {
+          // the copies never completed: flag it, let the other stages' copies
+          // land (bounded), and leave the stream
+          if (lane == 0) atomicExch(&a.stats->error, 1);
 #pragma unroll
-      for (int sidx = 0; sidx < kStages; ++sidx) {
-        if (stop) break;
-        const int64_t tile = q[sidx];
-        if (tile < 0) {
-          stop = true;
+          for (int o = 1; o < kStages; ++o) {
+            const int so = (stage + o) % kStages;
+            if (q[o] >= 0 && whole(q[o])) mbar_wait(my_bars + so, (phase >> so) & 1u);
+          }
           break;
         }
-        const int64_t first = tile * kTile;
-        if (whole(tile)) {
-          if (!mbar_wait(my_bars + sidx, (phase >> sidx) & 1u)) {
-            // the copies never completed: flag it, let the other stage's copy
-            // land (bounded), and leave the stream
-            if (lane == 0) atomicExch(&a.stats->error, 1);
-#pragma unroll
-            for (int o = 0; o < kStages; ++o)
-              if (o != sidx && q[o] >= 0 && whole(q[o])) mbar_wait(my_bars + o, (phase >> o) & 1u);
-            stop = true;
-            break;
-          }
-          phase ^= 1u << sidx;
-        }
-        // one call site of stream_one: staged tiles from shared memory, the
-        // rest (the array's tail, unaligned arrays) by plain loads
-        const bool staged = whole(tile);
-        const Tile& T = my_tiles[sidx];
-#pragma unroll 1
-        for (int r = 0; r < kTile / 32; ++r) {
-          const int j = r * 32 + lane;
-          const uint32_t i = (uint32_t)first + (uint32_t)j;
-          uint8_t st;
-          MixedState s;
-          if (staged) {
-            st = T.st[j];
-            s = MixedState{T.cell[j], T.frac[j], T.px[j], T.py[j], T.pz[j]};
-          } else {
-            fetch_stream(a, i, st, s);
-          }
-          stream_one(i, st, s);
-        }
-        __syncwarp();  // every lane is done with the stage before it is refilled
-        q[sidx] = gen();
-        issue(sidx, q[sidx]);
+        phase ^= 1u << stage;
       }
+      // one call site of stream_one: staged tiles from shared memory, the
+      // rest (the array's tail, unaligned arrays) by plain loads
+      const Tile& T = my_tiles[stage];
+#pragma unroll 1
+      for (int r = 0; r < kTile / 32; ++r) {
+        const int j = r * 32 + lane;
+        const uint32_t i = (uint32_t)first + (uint32_t)j;
+        uint8_t st;
+        MixedState s;
+        if (staged) {
+          st = T.st[j];
+          s = MixedState{T.cell[j], T.frac[j], T.px[j], T.py[j], T.pz[j]};
+        } else {
+          fetch_stream(a, i, st, s);
+        }
+        stream_one(i, st, s);
+      }
+      __syncwarp();  // every lane is done with the stage before it is refilled
+      const int64_t next = gen();
+      issue(stage, next);
+#pragma unroll
+      for (int o = 0; o + 1 < kStages; ++o) q[o] = q[o + 1];
+      q[kStages - 1] = next;
+      stage = stage + 1 == kStages ? 0 : stage + 1;
     }
   }
 
@@ -715,6 +719,16 @@ static cudaError_t launch_binned_p(const PushArgsMixed& a, int sm_count, cudaStr
     cudaError_t e = cudaFuncSetAttribute(push_binned_kernel<P, RING>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBinnedSmem);
     if (e != cudaSuccess) return e;
+#ifdef PIC_MIN_CARVEOUT
+    {  // the smallest shared-memory carveout that holds the resident blocks: the rest is L1
+      const int need = PIC_BINNED_MIN_BLOCKS * ((int)kBinnedSmem + 1024 + 512);
+      int pct = (need * 100 + 228 * 1024 - 1) / (228 * 1024);
+      if (pct > 100) pct = 100;
+      e = cudaFuncSetAttribute(push_binned_kernel<P, RING>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+      if (e != cudaSuccess) return e;
+    }
+#endif
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, push_binned_kernel<P, RING>, kThreads,
                                                   kBinnedSmem);
     if (occ < 1) occ = 1;
