@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--predict-every", type=int, default=64)
+    ap.add_argument("--heavy-budget", type=int, default=0,
+                    help="sub-steps of long sub-cycles per particle and launch (0: library default)")
     ap.add_argument("--batched-steps", type=int, default=200)
     ap.add_argument("--batched-ensembles", type=int, default=512)
     ap.add_argument("--cpu-sample", type=int, default=16384)
@@ -358,7 +360,7 @@ def run_ours(args, ws, rank, local):
     def make(precision, schedule, levels_upto):
         integ = native.Integrator(wl.dt, wl.dx, wl.psi_max, order=p, precision=precision,
                                   schedule=schedule, capacity=n_e, window=wl.window,
-                                  ring_levels=ring, stream=stream)
+                                  ring_levels=ring, stream=stream, heavy_budget=args.heavy_budget)
         integ.pic_particles_write(ini.x, ini.px, ini.py, ini.pz)
         for r in range(levels_upto + p):
             integ.pic_fields_upload(r - p, int(i0[r]), E[r], B[r])
