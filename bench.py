@@ -612,6 +612,12 @@ def main():
     # algorithmic bytes of the mixed push per particle-step: cell i32 + frac f32 +
     # p 3 x f32 + status u8, read and written
     bytes_per = 2 * (4 + 4 + 12 + 1)
+    # DRAM bytes (read + write) per electron-step of the push kernel, from one ncu
+    # capture (dram__bytes_read.sum + dram__bytes_write.sum = 183.8 + 161.1 MB) of an
+    # 8,388,608-electron launch at step 2454 of this workload; traffic grows with
+    # the electron count, so it is scaled to the launch timed here.  Re-measure
+    # whenever the kernel changes.
+    traffic_per = (183.8e6 + 161.1e6) / 8388608
     kern_ms = out["learned"]["kern_ms"] if "learned" in out else out["kern_ms"]
     achieved = bytes_per * wl.n_particles / (kern_ms / 1e3) / 1e9
     headline = out.get("learned", {"value": out["value"], "ms_per_step": out["ms_per_step"]})
@@ -637,7 +643,9 @@ def main():
         "speedup_vs_fp64": (headline["value"] / out["fp64_value"]) if out.get("fp64_value") else None,
         "accuracy": out.get("accuracy"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
+                     "frac": achieved / hbm,
+                     "traffic": traffic_per * wl.n_particles if wl.order == 3 else None,
+                     "traffic_note": "ncu DRAM bytes of an 8.4M-electron launch, scaled per electron",
                      "peak_source": peak_src, "kernel": "push_binned_kernel<3>",
                      "kernel_ms_per_launch": kern_ms,
                      "bytes_per_particle_step": bytes_per},
