@@ -164,6 +164,72 @@ __device__ __forceinline__ void boris_f32(float ey, float bz, float hp, float hx
   s.frac = __fmaf_rn(hx, __fmul_rn(ux, inv_g), s.frac);
 }
 
+// ---------------------------------------------------------------- two particles per lane
+//
+// The same arithmetic on two particles at once with GB300's paired FP32
+// instructions (mul/add/fma.rn.f32x2, written as PTX): each half rounds
+// exactly as the scalar operation it replaces.  a - b is fma(b, -1, a).  A
+// paired product that only paired sums consume can still be merged into them
+// by the compiler, so such a product is kept scalar (see boris_f32x2).
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " mul.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " add.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " mov.b64 rc, {%6, %7};\n fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return fma2(b, bc2(-1.0f), a); }
+__device__ __forceinline__ float2 floor2(float2 a) { return make_float2(floorf(a.x), floorf(a.y)); }
+
+struct MixedState2 {
+  int2 cell;
+  float2 frac, ux, uy, uz;
+};
+
+// boris_f32 on two particles (same operation order, same bits).
+__device__ __forceinline__ void boris_f32x2(float2 ey, float2 bz, float2 hp, float hx, float qm,
+                                            MixedState2& s) {
+  const float2 qmh = mul2(bc2(qm), mul2(bc2(0.5f), hp));
+  const float2 dpy = make_float2(__fmul_rn(qmh.x, ey.x), __fmul_rn(qmh.y, ey.y));
+  const float2 mx = s.ux, mz = s.uz;
+  const float2 g2xz = add2(bc2(1.0f), fma2(mz, mz, mul2(mx, mx)));
+  const float2 my = add2(s.uy, dpy);
+  const float2 gn = fma2(my, my, g2xz);
+  const float2 inv_gn = make_float2(rsqrt_sfu(gn.x), rsqrt_sfu(gn.y));
+  const float2 tz = mul2(mul2(qmh, bz), inv_gn);
+  const float2 ppx = fma2(my, tz, mx);
+  const float2 ppy = fma2(make_float2(-mx.x, -mx.y), tz, my);
+  const float2 tt = fma2(tz, tz, bc2(1.0f));
+  const float2 sz = mul2(mul2(bc2(2.0f), tz), make_float2(rcp_sfu(tt.x), rcp_sfu(tt.y)));
+  const float2 ux = fma2(ppy, sz, mx);
+  const float2 uy = add2(fma2(make_float2(-ppx.x, -ppx.y), sz, my), dpy);
+  s.ux = ux;
+  s.uy = uy;
+  s.uz = mz;
+  const float2 g2n = add2(bc2(1.0f), fma2(mz, mz, mul2(ux, ux)));
+  const float2 g = fma2(uy, uy, g2n);
+  const float2 inv_g = make_float2(rsqrt_sfu(g.x), rsqrt_sfu(g.y));
+  s.frac = fma2(bc2(hx), mul2(ux, inv_g), s.frac);
+}
+
 // Reciprocal of prod_{k != j} (j - k), the denominator of L_{p,j} (Sec. VI).
 __host__ __device__ constexpr float lagrange_inv_den(int p, int j) {
   float d = 1.f;
@@ -680,7 +746,7 @@ constexpr int kWarps = kThreads / 32;
 #endif
 constexpr int kChunk = PIC_CHUNK;    // particles per stream item (kChunk / kTile tiles)
 constexpr int kStages = PIC_STAGES;  // staged tiles per warp (one in flight while one is pushed)
-static_assert(kChunk % kTile == 0 && kTile % 32 == 0, "a stream item is whole tiles of whole warps");
+static_assert(kChunk % kTile == 0 && kTile % 64 == 0, "a stream item is whole tiles of whole rounds");
 constexpr int kStashK = kDeferMin - 1;
 constexpr int kStashCap = 64;
 constexpr uint8_t kParity = 0x08;

@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(256) push_mixed_plain_kernel(PushArgsMixed a) 
 //     and leaves the queue; a wrong prediction costs one idle lane.
 //  3. stream chunks of kChunk particles, staged into shared memory tile by
 //     tile with bulk copies (one tile in flight while another is pushed),
-//     one particle per lane.  k = 0: pushed at once (the
+//     two particles per lane per round.  k = 0: pushed at once (the
 //     criterion's B_z serves the push).  k = 1, 2: parked in the warp's stash
 //     for that k (shared memory); whenever a stash holds 32 particles the warp
 //     pushes them together, so short sub-cycles never diverge a warp and never
@@ -445,61 +445,142 @@ __global__ void __launch_bounds__(kThreads, PIC_BINNED_MIN_BLOCKS) push_binned_k
     if (full) drain(false);
   };
 
-  // one stream particle: criterion, then push (k = 0), park (k = 1, 2) or
-  // defer (k >= kDeferMin).  Warp-collective.  A round in which every lane's
-  // particle takes k = 0 (or is not the stream's) -- nearly all of them --
-  // skips the cap test, the queues and the stashes.
   constexpr uint8_t kStreamMask = PIC_STATUS_LOST | kDeferMask | kParity;
-  auto stream_one = [&](uint32_t i, uint8_t st, MixedState s) {
-    const bool mine = (st & kStreamMask) == want;  // lost (and so i >= n) excluded
-    int32_t je = 0, jb = 0;
-    float we = 0.f, wb = 0.f, b0 = 0.f, ey = 0.f;
-    bool inwin = false, push = false;
-    if (mine) {
-      inwin = tent_coords(s.cell, s.frac, F.lo, F.hi, je, we, jb, wb);
-      if (a.halfE) {
-        b0 = half_lerp(a.halfB, jb, wb, a.mask);
-        ey = half_lerp(a.halfE, je, we, a.mask);
-      } else {
-        b0 = gather_f32<P>(F.B, wcrit, jb, wb, a.mask);
-        ey = gather_f32<P>(F.E, w0, je, we, a.mask);
-      }
-      float a2, rhs;
-      psi_terms(b0, s, a.qm_abs, a.dt, a.psi_max, a2, rhs);
-      push = inwin && !(a2 > rhs);  // psi_to_k's k = 0 without a cap
+  // One stream round of 64 particles, two per lane (particles first+2q and
+  // first+2q+1, q = 32 r + lane), from the staged tile or, for the array's
+  // tail and unaligned arrays, from global memory: the criterion, then push
+  // (k = 0), park (k = 1, 2) or defer (k >= kDeferMin).  The k = 0 arithmetic
+  // runs on both particles at once with paired FP32 instructions (the bits of
+  // boris_f32, so the same bits as the other schedules).  A round in which
+  // every particle takes k = 0 (or is not the stream's) -- nearly all of them
+  // -- skips the cap test, the queues and the stashes.  Warp-collective.
+  const float qm_dt = __fmul_rn(a.qm_abs, a.dt);
+  const float tp = __fmul_rn(2.0f, a.psi_max);
+  const float tp2 = __fmul_rn(tp, tp);
+  auto stream_pair = [&](const Tile& T, bool staged, int r, uint32_t first) {
+    const int q = r * 32 + lane;
+    const uint32_t i = first + 2u * (uint32_t)q;
+    uint8_t st0, st1;
+    MixedState2 s;
+    if (staged) {
+      const uint32_t st2 = reinterpret_cast<const uint16_t*>(T.st)[q];
+      st0 = (uint8_t)st2;
+      st1 = (uint8_t)(st2 >> 8);
+      s.cell = reinterpret_cast<const int2*>(T.cell)[q];
+      s.frac = reinterpret_cast<const float2*>(T.frac)[q];
+      s.ux = reinterpret_cast<const float2*>(T.px)[q];
+      s.uy = reinterpret_cast<const float2*>(T.py)[q];
+      s.uz = reinterpret_cast<const float2*>(T.pz)[q];
+    } else {
+      MixedState u0, u1;
+      fetch_stream(a, i, st0, u0);  // past the end: lost
+      fetch_stream(a, i + 1, st1, u1);
+      s.cell = make_int2(u0.cell, u1.cell);
+      s.frac = make_float2(u0.frac, u1.frac);
+      s.ux = make_float2(u0.ux, u1.ux);
+      s.uy = make_float2(u0.uy, u1.uy);
+      s.uz = make_float2(u0.uz, u1.uz);
     }
-    const int k_prev = st & 7;
-    const bool fast = __all_sync(0xffffffffu, push || !mine);
-    int key = 0, sk = 0;
-    if (fast) {
-      tc.k0 += push ? 1u : 0u;
-    } else if (mine) {
-      if (!inwin) {
-        a.status[i] = (uint8_t)(st | PIC_STATUS_LOST);
-        atomicAdd(&sh[11], 1ull);
-      } else {
+    const bool mine0 = (st0 & kStreamMask) == want, mine1 = (st1 & kStreamMask) == want;
+    const float2 fe = floor2(s.frac);  // tent_coords of each
+    const float2 fbm = add2(s.frac, bc2(-0.5f));
+    const float2 fb = floor2(fbm);
+    const float2 we = sub2(s.frac, fe), wb = sub2(fbm, fb);
+    const int32_t je0 = s.cell.x + (int32_t)fe.x, je1 = s.cell.y + (int32_t)fe.y;
+    const int32_t jb0 = s.cell.x + (int32_t)fb.x, jb1 = s.cell.y + (int32_t)fb.y;
+    const bool in0 = jb0 >= F.lo && je0 < F.hi, in1 = jb1 >= F.lo && je1 < F.hi;
+    float2 ey, bz;  // half_lerp of each, or gather_f32 without half-step fields
+    if (a.halfE) {
+      const float* e0 = a.halfE + (je0 & a.mask);
+      const float* e1 = a.halfE + (je1 & a.mask);
+      const float* b0 = a.halfB + (jb0 & a.mask);
+      const float* b1 = a.halfB + (jb1 & a.mask);
+      const float2 elo = make_float2(__ldg(e0), __ldg(e1));
+      const float2 ehi = make_float2(__ldg(e0 + 1), __ldg(e1 + 1));
+      const float2 blo = make_float2(__ldg(b0), __ldg(b1));
+      const float2 bhi = make_float2(__ldg(b0 + 1), __ldg(b1 + 1));
+      ey = fma2(we, sub2(ehi, elo), elo);
+      bz = fma2(wb, sub2(bhi, blo), blo);
+    } else {
+      ey = make_float2(gather_f32<P>(F.E, w0, je0, we.x, a.mask),
+                       gather_f32<P>(F.E, w0, je1, we.y, a.mask));
+      bz = make_float2(gather_f32<P>(F.B, wcrit, jb0, wb.x, a.mask),
+                       gather_f32<P>(F.B, wcrit, jb1, wb.y, a.mask));
+    }
+    const float2 av = mul2(bc2(qm_dt), bz);  // psi_terms of each
+    const float2 a2 = mul2(av, av);
+    const float2 rhs =
+        mul2(bc2(tp2), add2(bc2(1.0f), fma2(s.uz, s.uz, fma2(s.uy, s.uy, mul2(s.ux, s.ux)))));
+    bool push0 = mine0 && in0 && !(a2.x > rhs.x);
+    bool push1 = mine1 && in1 && !(a2.y > rhs.y);
+    tc.k0 += (push0 ? 1u : 0u) + (push1 ? 1u : 0u);
+    const bool side = !__all_sync(0xffffffffu, (push0 || !mine0) && (push1 || !mine1));
+    int key0 = 0, key1 = 0, sk0 = 0, sk1 = 0;
+    if (side) {  // the rest of the criterion for the particles that do not take k = 0 at once
+#pragma unroll 1
+      for (int e = 0; e < 2; ++e) {
+        const bool mine = e ? mine1 : mine0;
+        bool& push = e ? push1 : push0;
+        const bool inwin = e ? in1 : in0;
+        const uint8_t st = e ? st1 : st0;
+        const uint32_t ii = i + (uint32_t)e;
+        int& key = e ? key1 : key0;
+        int& sk = e ? sk1 : sk0;
+        if (!mine || push) continue;
+        if (!inwin) {
+          a.status[ii] = (uint8_t)(st | PIC_STATUS_LOST);
+          atomicAdd(&sh[11], 1ull);
+          continue;
+        }
         bool capped;
-        const int k = psi_to_k(b0, s, a.qm_abs, a.dt, a.psi_max, a.k_max, capped);
+        const MixedState one = {0, 0.f, e ? s.ux.y : s.ux.x, e ? s.uy.y : s.uy.x, e ? s.uz.y : s.uz.x};
+        const int k = psi_to_k(e ? bz.y : bz.x, one, a.qm_abs, a.dt, a.psi_max, a.k_max, capped);
         count_step(tc, sh, k, capped);
-        push = k == 0;
-        if (k >= kDeferMin) {
-          defer_mark(a, i, k_prev, k, a.step_cur);
+        if (k == 0) {
+          push = true;  // capped at k_max = 0
+        } else if (k >= kDeferMin) {
+          defer_mark(a, ii, st & 7, k, a.step_cur);
           key = k;
-        } else if (k > 0) {
+        } else {
           sk = k;
         }
       }
     }
-    if (push) {
-      const float hp = __fmul_rn(0.5f, __fadd_rn(pow4_down(a.dt, k_prev), a.dt));
-      boris_f32(ey, b0, hp, hx0, a.qm, s);
-      normalize(s);
-      store_stream(a, i, s);
-      a.status[i] = done;
+    const MixedState p0 = {s.cell.x, s.frac.x, s.ux.x, s.uy.x, s.uz.x};  // as loaded, for the stash
+    const MixedState p1 = {s.cell.y, s.frac.y, s.ux.y, s.uy.y, s.uz.y};
+    if (push0 || push1) {
+      const float2 h_old = make_float2(pow4_down(a.dt, st0 & 7), pow4_down(a.dt, st1 & 7));
+      const float2 hp = mul2(bc2(0.5f), add2(h_old, bc2(a.dt)));
+      MixedState2 u = s;
+      boris_f32x2(ey, bz, hp, hx0, a.qm, u);
+      const float2 fl = floor2(u.frac);  // normalize each
+      u.cell.x += (int32_t)fl.x;
+      u.cell.y += (int32_t)fl.y;
+      u.frac = sub2(u.frac, fl);
+      if (push0 && push1 && a.tma) {  // 16-byte aligned arrays, i even: 8-byte stores
+        __stcs(reinterpret_cast<int2*>(a.cell + i), u.cell);
+        __stcs(reinterpret_cast<float2*>(a.frac + i), u.frac);
+        __stcs(reinterpret_cast<float2*>(a.px + i), u.ux);
+        __stcs(reinterpret_cast<float2*>(a.py + i), u.uy);
+        __stcs(reinterpret_cast<float2*>(a.pz + i), u.uz);
+        *reinterpret_cast<uint16_t*>(a.status + i) = (uint16_t)(done | (done << 8));
+      } else {
+        if (push0) {
+          store_stream(a, i, MixedState{u.cell.x, u.frac.x, u.ux.x, u.uy.x, u.uz.x});
+          a.status[i] = done;
+        }
+        if (push1) {
+          store_stream(a, i + 1, MixedState{u.cell.y, u.frac.y, u.ux.y, u.uy.y, u.uz.y});
+          a.status[i + 1] = done;
+        }
+      }
     }
-    if (!fast) {
-      enqueue(a, key, (int32_t)i);
-      park(sk, (int32_t)i, s, (uint8_t)k_prev);
+    if (side) {
+#pragma unroll 1
+      for (int e = 0; e < 2; ++e) {
+        enqueue(a, e ? key1 : key0, (int32_t)(i + (uint32_t)e));
+        park(e ? sk1 : sk0, (int32_t)(i + (uint32_t)e), e ? p1 : p0, (uint8_t)((e ? st1 : st0) & 7));
+      }
     }
   };
 
@@ -605,23 +686,10 @@ __global__ void __launch_bounds__(kThreads, PIC_BINNED_MIN_BLOCKS) push_binned_k
         }
         phase ^= 1u << stage;
       }
-      // one call site of stream_one: staged tiles from shared memory, the
-      // rest (the array's tail, unaligned arrays) by plain loads
-      const Tile& T = my_tiles[stage];
+      // rounds of 64 particles (stream_pair's one call site): staged tiles from
+      // shared memory, the rest (the array's tail, unaligned arrays) by plain loads
 #pragma unroll 1
-      for (int r = 0; r < kTile / 32; ++r) {
-        const int j = r * 32 + lane;
-        const uint32_t i = (uint32_t)first + (uint32_t)j;
-        uint8_t st;
-        MixedState s;
-        if (staged) {
-          st = T.st[j];
-          s = MixedState{T.cell[j], T.frac[j], T.px[j], T.py[j], T.pz[j]};
-        } else {
-          fetch_stream(a, i, st, s);
-        }
-        stream_one(i, st, s);
-      }
+      for (int r = 0; r < kTile / 64; ++r) stream_pair(my_tiles[stage], staged, r, (uint32_t)first);
       __syncwarp();  // every lane is done with the stage before it is refilled
       const int64_t next = gen();
       issue(stage, next);
