@@ -134,6 +134,89 @@ def test_fp64_full_c1_sampled():
     assert gst.out_of_window == (~kept).sum() and kept.any()
 
 
+@pytest.mark.parametrize("k_max,psi_max", [(0, 0.01), (7, 1e30)])
+def test_fp64_bitwise_degenerate_criterion(k_max, psi_max):
+    """The criterion's degenerate ends: k_max = 0 (no sub-cycling; every step
+    past the threshold counted as capped) and Psi_max = 1e30 (the criterion
+    never fires): both reduce to the standard PIC push of Sec. III, bit for
+    bit, counters included."""
+    wl = _c1(300, psi_max=psi_max)
+    g, gst = _gpu_run(wl, 400, native.PIC_FP64, k_max=k_max)
+    o, ost = _oracle_run(wl, 400, k_max=k_max)
+    _assert_bitwise(g, o, gst, ost)
+    assert gst.k_hist[0] == sum(gst.k_hist) and gst.substeps == gst.k_hist[0]
+    assert (gst.clamped > 0) == (k_max == 0)
+
+
+@pytest.mark.parametrize("k_max,psi_max", [(0, 0.01), (7, 1e30)])
+def test_mixed_binned_bitwise_plain_degenerate_criterion(k_max, psi_max):
+    wl = _c1(300, psi_max=psi_max)
+    a, sa = _gpu_run(wl, 400, native.PIC_MIXED, k_max=k_max, schedule=native.PIC_SCHED_PLAIN)
+    b, sb = _gpu_run(wl, 400, native.PIC_MIXED, k_max=k_max, schedule=native.PIC_SCHED_BINNED)
+    for u, v in zip(a, b):
+        np.testing.assert_array_equal(u, v)
+    assert list(sa.k_hist) == list(sb.k_hist) and sa.clamped == sb.clamped
+
+
+def test_empty_particle_set():
+    """No electrons loaded: every form and schedule steps through the levels,
+    launches nothing that touches particles, and reports zero counts."""
+    wl = _c1(8)
+    for precision, schedule in ((native.PIC_FP64, native.PIC_SCHED_PLAIN),
+                                (native.PIC_MIXED, native.PIC_SCHED_PLAIN),
+                                (native.PIC_MIXED, native.PIC_SCHED_BINNED)):
+        integ = H.gpu_integrator(wl, precision, schedule=schedule, capacity=8)
+        z = np.empty(0)
+        integ.pic_particles_write(z, z, z, z)
+        st = H.GpuRun(integ, wl, wl.order).run(0, 20)
+        assert sum(st.k_hist) == 0 and st.substeps == 0 and st.out_of_window == 0
+        assert all(len(a) == 0 for a in integ.read_numpy())
+        integ.close()
+
+
+def test_full_size_headline_workload_sampled():
+    """The 16,777,216-electron a0 = 150 Maxwellian workload at full size and in
+    the launch configuration the benchmark times (one multi-step call over a ring
+    holding every level, binned mixed schedule), through its first 120 steps while
+    the front sweeps the first electrons.  The FP64 form is checked against the
+    oracle bit for bit on electrons the oracle recomputes one by one (the first
+    ones, which the front hits and which sub-cycle, and random ones); the binned
+    mixed form is checked against the FP64 form on every electron."""
+    wl = W.C2
+    p, K = wl.order, 120
+    E, B, i0 = wl.levels(-p, K + p)
+    ini = wl.particles()
+
+    def run(precision, schedule):
+        integ = native.Integrator(wl.dt, wl.dx, wl.psi_max, order=p, precision=precision,
+                                  schedule=schedule, capacity=wl.n_particles, window=wl.window,
+                                  ring_levels=K + p + 1)
+        integ.pic_particles_write(ini.x, ini.px, ini.py, ini.pz)
+        for r in range(K + p):
+            integ.pic_fields_upload(r - p, int(i0[r]), E[r], B[r])
+        st, _ = integ.pic_push_step(0, K, want_stats=True, ok=P_OK_OR_RANGE)
+        out = integ.read_numpy()
+        integ.close()
+        return out, st
+
+    g64, st64 = run(native.PIC_FP64, native.PIC_SCHED_PLAIN)
+    gmx, stmx = run(native.PIC_MIXED, native.PIC_SCHED_BINNED)
+    assert st64.k_hist[5] > 0, "the front must reach the first electrons"
+    idx = np.concatenate([np.arange(48),
+                          np.random.default_rng(5).choice(wl.n_particles, 48, replace=False)])
+    o, _ = _oracle_run(wl, K, idx=idx)
+    _assert_bitwise(tuple(a[idx] for a in g64), o)
+    _, px, py, pz, _ = gmx
+    _, qx, qy, qz, _ = g64
+    dp = np.max(np.abs(np.stack([px - qx, py - qy, pz - qz])), axis=0) / wl.a0 ** 2
+    gam_m = np.sqrt(1 + px ** 2 + py ** 2 + pz ** 2) - 1
+    gam_f = np.sqrt(1 + qx ** 2 + qy ** 2 + qz ** 2) - 1
+    de = abs(gam_m.mean() - gam_f.mean()) / gam_f.mean()
+    assert de <= 1e-3, de
+    assert (dp > 1e-4).mean() <= 0.005, (dp.max(), (dp > 1e-4).sum())
+    assert abs(stmx.substeps - st64.substeps) <= 0.01 * st64.substeps
+
+
 # ---------------------------------------------------------------- mixed form: within budget
 
 def _mixed_errors(g, o, a0, x0):
