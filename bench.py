@@ -613,11 +613,11 @@ def main():
     # p 3 x f32 + status u8, read and written
     bytes_per = 2 * (4 + 4 + 12 + 1)
     # DRAM bytes (read + write) per electron-step of the push kernel, from one ncu
-    # capture (dram__bytes_read.sum + dram__bytes_write.sum = 183.9 + 165.7 MB) of an
+    # capture (dram__bytes_read.sum + dram__bytes_write.sum = 184.7 + 166.1 MB) of an
     # 8,388,608-electron launch at step 2454 of this workload; traffic grows with
     # the electron count, so it is scaled to the launch timed here.  Re-measure
     # whenever the kernel changes.
-    traffic_per = (183.9e6 + 165.7e6) / 8388608
+    traffic_per = (184.7e6 + 166.1e6) / 8388608
     kern_ms = out["learned"]["kern_ms"] if "learned" in out else out["kern_ms"]
     achieved = bytes_per * wl.n_particles / (kern_ms / 1e3) / 1e9
     headline = out.get("learned", {"value": out["value"], "ms_per_step": out["ms_per_step"]})

@@ -224,12 +224,16 @@ __global__ void batch_prefix_kernel(const int32_t* qcount_in, int32_t n_ens, int
   if (threadIdx.x == blockDim.x - 1) prefix[n] = acc;
 }
 
+// Block shape of the batched kernel (its own: two blocks of eight warps per SM).
+constexpr int kBatchThreads = 256;
+constexpr int kBatchWarps = kBatchThreads / 32;
+
 template <int P>
-__global__ void __launch_bounds__(kThreads, 2) push_batch_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(kBatchThreads, 2) push_batch_kernel(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  BatchStash* stashes = reinterpret_cast<BatchStash*>(smem);  // [kWarps][kStashK]
+  BatchStash* stashes = reinterpret_cast<BatchStash*>(smem);  // [kBatchWarps][kStashK]
   __shared__ unsigned long long sh[12];
-  __shared__ int s_task[kWarps];
+  __shared__ int s_task[kBatchWarps];
   if (threadIdx.x < 12) sh[threadIdx.x] = 0ull;
   __syncthreads();
   constexpr int stride = 2 * (P + 1);
@@ -394,7 +398,7 @@ __global__ void batch_reset_status_kernel(uint8_t* status, int64_t n) {
   }
 }
 
-constexpr size_t kBatchStashBytes = sizeof(BatchStash) * kWarps * kStashK;
+constexpr size_t kBatchStashBytes = sizeof(BatchStash) * kBatchWarps * kStashK;
 
 static_assert(kBatchStashBytes <= 48 * 1024, "stashes must fit the default shared-memory limit");
 
@@ -409,7 +413,7 @@ static cudaError_t launch_batch_p(const BatchArgs& a, int blocks, cudaStream_t s
     batch_halfstep_kernel<P><<<(int)(want < 152 * 16 ? want : 152 * 16), 256, 0, s>>>(a);
     ++n;
   }
-  push_batch_kernel<P><<<blocks, kThreads, kBatchStashBytes, s>>>(a);
+  push_batch_kernel<P><<<blocks, kBatchThreads, kBatchStashBytes, s>>>(a);
   if (a.finalize) {
     const int64_t want = (a.n_total + 255) / 256;
     batch_reset_status_kernel<<<(int)(want < 152 * 8 ? want : 152 * 8), 256, 0, s>>>(a.status,
@@ -436,11 +440,11 @@ cudaError_t launch_batch_step(const BatchArgs& a, int order, int blocks, cudaStr
 int batch_max_blocks_per_sm(int order) {
   int occ = 0;
   switch (order) {
-    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, push_batch_kernel<1>, kThreads, kBatchStashBytes); break;
-    case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, push_batch_kernel<2>, kThreads, kBatchStashBytes); break;
-    case 3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, push_batch_kernel<3>, kThreads, kBatchStashBytes); break;
-    case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, push_batch_kernel<4>, kThreads, kBatchStashBytes); break;
-    case 5: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, push_batch_kernel<5>, kThreads, kBatchStashBytes); break;
+    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, push_batch_kernel<1>, kBatchThreads, kBatchStashBytes); break;
+    case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, push_batch_kernel<2>, kBatchThreads, kBatchStashBytes); break;
+    case 3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, push_batch_kernel<3>, kBatchThreads, kBatchStashBytes); break;
+    case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, push_batch_kernel<4>, kBatchThreads, kBatchStashBytes); break;
+    case 5: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, push_batch_kernel<5>, kBatchThreads, kBatchStashBytes); break;
     default: break;
   }
   return occ > 0 ? occ : 1;
