@@ -325,10 +325,10 @@ constexpr size_t kStashBytes = sizeof(Stash) * kWarps * kStashK;
 constexpr size_t kBinnedSmem = kStashBytes + sizeof(Tile) * kWarps * kStages;
 static_assert(kStashBytes % 128 == 0, "tiles start on a 128-byte boundary");
 
-// Two resident blocks (16 warps) per SM: up to 128 registers a thread, and
-// fewer warps contending for the instruction cache across the kernel's
-// stream, stash and deferred-particle code (measured faster than three blocks
-// at 80 registers).
+// Two resident blocks per SM (of kThreads each): measured faster than three,
+// whose register cap costs instructions and whose extra warps contend for the
+// instruction cache across the kernel's stream, stash and deferred-particle
+// code.
 #ifndef PIC_BINNED_MIN_BLOCKS
 #define PIC_BINNED_MIN_BLOCKS 2
 #endif
