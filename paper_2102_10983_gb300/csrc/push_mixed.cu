@@ -19,16 +19,18 @@
 // Schedules:
 //  PLAIN:  one thread per particle; a warp runs as long as its largest 4^k.
 //  BINNED: one persistent kernel per macro step with an atomic work cursor.
-//          The bulk streams every particle with coalesced evict-first loads
-//          (one particle per lane, two rounds in flight); a particle whose
-//          criterion gives k = 0 is pushed at once, one with k > 0 is compacted
-//          (warp match + one atomic per k) into the queue of its k and its
-//          sub-cycling is deferred.  The first work items of the next step's
-//          kernel drain those queues, largest k first, in warps of equal k:
-//          each deferred particle finishes its previous step and then takes its
-//          own criterion for the current one.  So the long sub-cycled pushes
-//          run concurrently with the HBM stream of the next step instead of
-//          after it.  A closing kernel finishes what the last step deferred.
+//          The bulk streams every particle through tiles staged in shared
+//          memory by bulk copies (two particles per lane per round); a particle
+//          whose criterion gives k = 0 is pushed at once, one with k = 1, 2 is
+//          parked in a per-warp stash and pushed with 31 others, one with
+//          k >= 3 is compacted (warp match + one atomic per k) into the queue
+//          of its k and its sub-cycling is deferred.  The first work items of
+//          the next step's kernel drain those queues, largest k first, in warps
+//          of equal k: each deferred particle finishes its previous step (at
+//          most a budget of sub-steps per launch) and then takes its own
+//          criterion for the current one.  So the long sub-cycled pushes run
+//          concurrently with the HBM stream of the next step instead of after
+//          it.  A closing kernel finishes what the last step deferred.
 //
 // Status byte inside a binned call: bits 0-2 = k_prev, bit 3 = step parity
 // (the bulk of step j only takes particles whose parity equals j & 1 and flips
