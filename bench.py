@@ -55,8 +55,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--predict-every", type=int, default=64)
-    ap.add_argument("--heavy-budget", type=int, default=0,
-                    help="sub-steps of long sub-cycles per particle and launch (0: library default)")
+    ap.add_argument("--heavy-budget", type=int, default=512,
+                    help="sub-steps of long sub-cycles per particle and launch (0: library default, 256)")
     ap.add_argument("--batched-steps", type=int, default=200)
     ap.add_argument("--batched-ensembles", type=int, default=512)
     ap.add_argument("--cpu-sample", type=int, default=16384)

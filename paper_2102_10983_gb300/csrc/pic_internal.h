@@ -14,7 +14,10 @@ constexpr int kMaxK = 7;
 // Binned schedule: smallest k whose sub-cycle is deferred to the next launch's
 // first work items (shorter ones are compacted inside the warp); also the
 // smallest predicted k the predicted schedule bins before a launch.
-constexpr int kDeferMin = 3;
+#ifndef PIC_DEFER_MIN
+#define PIC_DEFER_MIN 3
+#endif
+constexpr int kDeferMin = PIC_DEFER_MIN;
 // Predicted schedule: smallest predicted k that puts a particle in the
 // predicted queue.  The long sub-cycles only: binning the short ones too (1)
 // took them out of the stream's stashes but measured slower, the network
