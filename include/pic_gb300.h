@@ -171,6 +171,13 @@ int pic_timing_enable(pic_ctx* ctx, int32_t on);
  * since the last reset; synchronizes the stream.  Errors: PIC_EINVAL, PIC_ECUDA. */
 int pic_timing_read(pic_ctx* ctx, double* total_ms, int64_t* steps, int32_t reset);
 
+/* Set the context's device error word to `word` (queued on the stream), as
+ * the give-up path of a bounded device wait does, so that a host program (or
+ * a test) can check its handling of PIC_ETIMEOUT without making a device wait
+ * run out.  The next pic_push_step with stats, or pic_stats_read, reports it.
+ * Errors: PIC_EINVAL, PIC_ECUDA. */
+int pic_inject_error(pic_ctx* ctx, int32_t word);
+
 /* Number of kernel launches the context has queued since creation. */
 int64_t pic_launch_count(const pic_ctx* ctx);
 
@@ -302,8 +309,8 @@ const char* pic_batch_last_error(const pic_batch* b);
  * in the paper: it exists for host programs that may not call cudaMalloc at
  * push time, e.g. because another framework owns and carves up all device
  * memory, or because a real-time loop must avoid the allocator).  The caller
- * owns every input and output; the weight table, per-k queues, work cursor
- * and counters live in one fixed file-scope __device__ array of ~6.8 MB that
+ * owns every input and output; the weight tables, per-k queues, work cursor
+ * and counters live in one fixed file-scope __device__ array of ~12.8 MB that
  * every GPU loading the library holds until the process exits.  Nothing is
  * allocated: no cudaMalloc/cudaFree, no allocating library call.
  *
@@ -324,14 +331,23 @@ const char* pic_batch_last_error(const pic_batch* b);
  *  stream:     cudaStream_t (or NULL); all work is queued on it.
  *  stats:      optional; if non-NULL the stream is synchronized and the
  *              counters of this call are returned (PIC_ERANGE / PIC_EKMAX as
- *              for pic_push_step).
- * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress) and builds the weight table there, so make that first
- * call before any stream capture.  Every call shares the array and finds the
- * previous call's contents; the call clears what must start at zero.  Calls
- * that run concurrently on the GPU (other streams, other host threads) race
- * on the array and must be serialized by the caller.
- * Errors: PIC_EINVAL, PIC_ECUDA, PIC_ERANGE, PIC_EKMAX. */
+ *              for pic_push_step).  With stats == NULL nothing synchronizes
+ *              (except a first call per key, below).
+ * Set-up: the first call on a device looks up the scratch array's device
+ * address (cudaGetSymbolAddress); the first call with each (order,
+ * field_time) builds that pair's weight table in the array and synchronizes
+ * the stream once.  Make those first calls before any stream capture.  Tables
+ * are never rewritten, so changing the parameters between calls is safe.
+ * Every call shares the array and finds the previous call's contents; the
+ * call clears what must start at zero.  Calls that run concurrently on the GPU
+ * (other streams, other host threads) race on the array and must be
+ * serialized by the caller.
+ * A bounded device wait that gives up (PIC_ETIMEOUT) leaves part of the
+ * particles unpushed.  It sets an error word in the array that stays set
+ * until a call with stats != NULL reports it, so the give-up of an
+ * asynchronous call (stats == NULL) is returned by the next call that passes
+ * stats.
+ * Errors: PIC_EINVAL, PIC_ECUDA, PIC_ERANGE, PIC_EKMAX, PIC_ETIMEOUT. */
 int pic_push_mixed_noalloc(const pic_params* prm, int64_t n_particles, int32_t* cell,
                            float* frac, float* px, float* py, float* pz, uint8_t* status,
                            const float* const* Ey_levels, const float* const* Bz_levels,

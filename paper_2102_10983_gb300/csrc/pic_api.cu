@@ -500,6 +500,14 @@ static int collect_stats(pic_ctx* c, pic_step_stats* out, bool reset) {
   return PIC_OK;
 }
 
+extern "C" int pic_inject_error(pic_ctx* c, int32_t word) {
+  if (!c) return PIC_EINVAL;
+  // pageable source: the copy is staged before cudaMemcpyAsync returns
+  CUDA_TRY(c, cudaMemcpyAsync(&c->dstats->error, &word, sizeof(int32_t), cudaMemcpyHostToDevice,
+                              c->stream));
+  return PIC_OK;
+}
+
 extern "C" int pic_stats_read(pic_ctx* c, pic_step_stats* stats, int32_t reset) {
   if (!c || !stats) return PIC_EINVAL;
   int rc = collect_stats(c, stats, reset != 0);

@@ -676,11 +676,15 @@ __global__ void __launch_bounds__(kThreads, PIC_BINNED_MIN_BLOCKS) push_binned_k
       const bool staged = whole(tile);
       if (staged) {
         if (!mbar_wait(my_bars + stage, (phase >> stage) & 1u)) {
-          // the copies never completed: flag it, let the other stages' copies
-          // land (bounded), and leave the stream
+          // The copies never completed: flag it for the host (PIC_ETIMEOUT)
+          // and leave the stream.  No instruction cancels a bulk copy, so
+          // before the block may exit, every stage this warp has in flight --
+          // this one included -- gets one more bounded wait: only a copy that
+          // has not landed after two full waits (a memory system that no
+          // longer answers) can outlive the block.
           if (lane == 0) atomicExch(&a.stats->error, 1);
 #pragma unroll
-          for (int o = 1; o < kStages; ++o) {
+          for (int o = 0; o < kStages; ++o) {
             const int so = (stage + o) % kStages;
             if (q[o] >= 0 && whole(q[o])) mbar_wait(my_bars + so, (phase >> so) & 1u);
           }

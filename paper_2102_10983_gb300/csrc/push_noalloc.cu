@@ -10,9 +10,10 @@
 // needs (weight table, per-k queues, counters, work cursor) in one file-scope
 // __device__ array of fixed size, so it never allocates.
 //
-// Cost of that choice: the array below (~6.8 MB) exists on every GPU that
+// Cost of that choice: the array below (~12.8 MB) exists on every GPU that
 // loads the library, from load until process exit, and all calls share it.
 #include <math.h>
+#include <stddef.h>
 #include <string.h>
 
 #include <mutex>
@@ -25,13 +26,23 @@ namespace {
 constexpr int64_t kNoAllocMaxParticles = 65536;
 constexpr int64_t kRows = (((int64_t)1 << (2 * (kMaxK + 1))) - 1) / 3 + 1;  // wrows_total(7)
 constexpr int64_t kMaxStride = 2 * (kMaxOrder + 1);
+// FP32 weight tables, one per (order p, field-time reading), each with the rows
+// of every k <= 7 (the rows of a smaller cap are a prefix of them) and a last
+// row holding the theta = 1/2 weights every cap's criterion uses.  A table is
+// built on the first call with its key and never rewritten, so work queued
+// with one key never reads another key's weights.  Table (p, ft) starts at
+// float ft * kRows * kSumStride + kRows * (p - 1)(p + 2).
+constexpr int64_t kSumStride = 2 * (2 + 3 + 4 + 5 + 6);  // sum over p = 1..5 of 2(p + 1)
+constexpr int64_t table_offset(int p, int ft) {
+  return ft * kRows * kSumStride + kRows * (int64_t)(p - 1) * (p + 2);
+}
 
 struct NoAllocScratch {
-  double wtab64[kRows * kMaxStride];
-  float wtab32[kRows * kMaxStride];
+  double wtab64[kRows * kMaxStride];  // build buffer of one table
+  float wtab32[2 * kRows * kSumStride];
   int32_t queue[2 * 7 * kNoAllocMaxParticles];
   int32_t qcount[64];  // [0,16): per-k counts of both queue sets; 16: cursor; 18: blocks done
-  DevStats stats;
+  DevStats stats;      // counters of the current call; the error word is kept until reported
 };
 
 // The scratch.  Host code must not use this name as an address: its device
@@ -42,10 +53,10 @@ constexpr int kMaxDevices = 64;
 struct DeviceSlot {
   NoAllocScratch* ptr = nullptr;  // device address of g_noalloc_scratch
   int sm_count = 0;
-  int wtab_key = -1;  // (order, k_max, field_time) the table was built for
+  bool built[2][kMaxOrder + 1] = {};  // weight table (field_time, order) is in place
 };
 DeviceSlot g_slots[kMaxDevices];
-std::mutex g_mutex;
+std::mutex g_mutex;  // guards g_slots
 
 thread_local char g_err[256];
 
@@ -55,13 +66,9 @@ int fail(int code, const char* msg) {
   return code;
 }
 
-// Once per device, with that device current: fetch the device address of the
-// scratch array.
-int scratch_on_current_device(DeviceSlot** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-    return fail(PIC_ECUDA, "pic_push_mixed_noalloc: no usable current CUDA device");
-  std::lock_guard<std::mutex> lock(g_mutex);
+// With the device current and g_mutex held: the device address of the
+// scratch array (looked up once per device).
+int scratch_on_current_device(int dev, DeviceSlot** out) {
   DeviceSlot& s = g_slots[dev];
   if (!s.ptr) {
     void* p = nullptr;
@@ -72,6 +79,23 @@ int scratch_on_current_device(DeviceSlot** out) {
     s.ptr = (NoAllocScratch*)p;
   }
   *out = &s;
+  return PIC_OK;
+}
+
+// With g_mutex held: the FP32 weight table of (p, ft), built on stream st and
+// waited for the first time it is asked for (so a build failure is seen here
+// and the table is complete before any later call can read it).
+int table_on_device(DeviceSlot& s, int p, int ft, cudaStream_t st, const float** out) {
+  NoAllocScratch* S = s.ptr;
+  float* t = S->wtab32 + table_offset(p, ft);
+  if (!s.built[ft][p]) {
+    cudaError_t e = build_wtab_f64(S->wtab64, p, kMaxK, ft, st);
+    if (e == cudaSuccess) e = build_wtab_f32(t, S->wtab64, kRows * 2 * (p + 1), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(PIC_ECUDA, cudaGetErrorString(e));
+    s.built[ft][p] = true;
+  }
+  *out = t;
   return PIC_OK;
 }
 
@@ -111,26 +135,28 @@ extern "C" int pic_push_mixed_noalloc(const pic_params* prm, int64_t n_particles
       return fail(PIC_EINVAL, "pic_push_mixed_noalloc: level window outside +-2^30 nodes");
   }
 
-  DeviceSlot* slot = nullptr;
-  int rc = scratch_on_current_device(&slot);
-  if (rc != PIC_OK) return rc;
-  NoAllocScratch* S = slot->ptr;
   cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return fail(PIC_ECUDA, "pic_push_mixed_noalloc: no usable current CUDA device");
+  DeviceSlot* slot = nullptr;
+  const float* wtab = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_mutex);
+    int rc = scratch_on_current_device(dev, &slot);
+    if (rc == PIC_OK) rc = table_on_device(*slot, p, prm->field_time, st, &wtab);
+    if (rc != PIC_OK) return rc;
+  }
+  NoAllocScratch* S = slot->ptr;
   auto cuda_fail = [](cudaError_t e) {
     return fail(PIC_ECUDA, cudaGetErrorString(e));
   };
   cudaError_t e;
-  // weight table for these parameters (rebuilt when they change)
-  const int key = (p * 8 + prm->k_max) * 2 + prm->field_time;
-  const int64_t wcount = wrows_total(prm->k_max) * 2 * (p + 1);
-  if (slot->wtab_key != key) {
-    if ((e = build_wtab_f64(S->wtab64, p, prm->k_max, prm->field_time, st)) != cudaSuccess) return cuda_fail(e);
-    if ((e = build_wtab_f32(S->wtab32, S->wtab64, wcount, st)) != cudaSuccess) return cuda_fail(e);
-    slot->wtab_key = key;
-  }
   // what must start at zero: queue counts, cursor, block counter, counters
+  // (not the error word: an asynchronous call's give-up stays set until a
+  // call with stats reports it)
   if ((e = cudaMemsetAsync(S->qcount, 0, sizeof(S->qcount), st)) != cudaSuccess) return cuda_fail(e);
-  if ((e = cudaMemsetAsync(&S->stats, 0, sizeof(DevStats), st)) != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaMemsetAsync(&S->stats, 0, offsetof(DevStats, error), st)) != cudaSuccess) return cuda_fail(e);
 
   const int64_t W = window_cells;
   auto window_of = [&](int64_t step, int64_t* lo, int64_t* hi) {
@@ -158,8 +184,8 @@ extern "C" int pic_push_mixed_noalloc(const pic_params* prm, int64_t n_particles
   base.k_max = prm->k_max;
   base.field_time = prm->field_time;
   lagrange_monomials(p, base.mono);
-  base.wtab = S->wtab32;
-  base.crit_row = wrows_total(prm->k_max) - 1;
+  base.wtab = wtab;
+  base.crit_row = kRows - 1;  // theta = 1/2, the same weights as the cap's own criterion row
   base.stats = &S->stats;
   base.qcap = kNoAllocMaxParticles;
   base.cursor = (int*)(S->qcount + 16);
@@ -219,6 +245,12 @@ extern "C" int pic_push_mixed_noalloc(const pic_params* prm, int64_t n_particles
   stats->clamped = (int64_t)h.clamped;
   stats->out_of_window = (int64_t)h.lost;
   stats->error = h.error;
+  if (h.error) {
+    if ((e = cudaMemsetAsync(&S->stats.error, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e);
+    return fail(PIC_ETIMEOUT, "pic_push_mixed_noalloc: a bounded device wait gave up (this call or an "
+                              "earlier one without stats); particle state is not trustworthy");
+  }
   if (stats->out_of_window) return fail(PIC_ERANGE, "particles left the field window");
   if (stats->clamped) return fail(PIC_EKMAX, "criterion capped at k_max");
   return PIC_OK;

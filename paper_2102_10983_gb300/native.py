@@ -65,6 +65,7 @@ SIGNATURES = {
     "pic_timing_enable": (ctypes.c_int, [_VP, _I32]),
     "pic_timing_read": (ctypes.c_int, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_I64), _I32]),
     "pic_launch_count": (ctypes.c_int64, [_VP]),
+    "pic_inject_error": (ctypes.c_int, [_VP, _I32]),
     "pic_last_error": (ctypes.c_char_p, [_VP]),
     "pic_features": (ctypes.c_int, [_VP, _I64, _VP]),
     "pic_predict": (ctypes.c_int, [_VP, _VP, _I64, _VP]),
@@ -239,6 +240,9 @@ class Integrator:
 
     def launches(self) -> int:
         return int(lib().pic_launch_count(self.ctx))
+
+    def inject_error(self, word: int = 1):
+        _check(lib().pic_inject_error(self.ctx, int(word)), self.ctx)
 
     # convenience: read everything to numpy
     def read_numpy(self):

@@ -127,9 +127,15 @@ def test_fp64_full_c1_sampled():
     idx = np.random.default_rng(0).choice(wl.n_particles, 12, replace=False)
     o, _ = _oracle_run(wl, wl.n_steps, idx=idx)
     _assert_bitwise(tuple(a[idx] for a in g), o)
-    # The switched-on front (E jumps from 0 to a0 at xi = 0) throws a few
-    # electrons far off the closed form; they trail out of the moving window and
-    # are frozen and counted (identically on both sides, checked above).
+    # The switched-on front (E jumps from 0 to a0 at xi = 0, and no grid
+    # resolves the jump) leaves the electrons with R = gamma - p_x spread far
+    # from the closed form's R = 1, in the method itself: the oracle, run on
+    # all 256 electrons, loses 152 out of the back of the moving window (large
+    # R: fast in xi) and ends the kept ones at R in [0.42, 1.59] and xi in
+    # [3.1, 7.1], not at xi >= 2 pi.  So the closed-form check of this
+    # configuration is not asserted here; it is pinned on the smooth pulse
+    # (test_plane_wave_closed_form_smooth_pulse).  What holds on this front:
+    # the same bits as the oracle (above), frozen electrons counted alike.
     kept = (g[4] & native.PIC_STATUS_LOST) == 0
     assert gst.out_of_window == (~kept).sum() and kept.any()
 

@@ -48,7 +48,12 @@ def test_zero_network_closed_forms():
     assert not np.any(g["W1"]) and not np.any(g["W2"])
 
 
-def test_features_are_the_stated_transform():
+def test_features_hand_computed():
+    """phi = (asinh|E_y|, asinh|B_z|, asinh p_x, asinh p_y, asinh p_z, log gamma)
+    at E_y = 3, B_z = -4, p = (0, 1, -2), against values worked out by hand from
+    asinh u = ln(u + sqrt(u^2 + 1)) and gamma = sqrt(1 + 0 + 1 + 4) = sqrt 6:
+    ln(3 + sqrt 10), ln(4 + sqrt 17), 0, ln(1 + sqrt 2), -ln(2 + sqrt 5), ln 6 / 2."""
     f = mlp.features([3.0], [-4.0], [0.0], [1.0], [-2.0])
-    np.testing.assert_allclose(f[0], [np.arcsinh(3.0), np.arcsinh(4.0), 0.0, np.arcsinh(1.0),
-                                      np.arcsinh(-2.0), np.log(np.sqrt(6.0))])
+    want = [1.8184464592320668, 2.0947125472611012, 0.0, 0.8813735870195430,
+            -1.4436354751788103, 0.8958797346140275]
+    np.testing.assert_allclose(f[0], want, rtol=1e-15, atol=0)

@@ -228,3 +228,83 @@ def test_second_order_convergence():
     e = [_smooth_run(2.0, 3, 1e30, res, n=4)["r_dev"].max() for res in (40, 80, 160)]
     for a, b in zip(e, e[1:]):
         assert 3.3 < a / b < 4.8, e
+
+
+# ---------------------------------------------------------------- sub-step field time (Sec. VI)
+
+def _linear_in_time_kicks(field_time: int, order: int):
+    """Two macro steps of a uniform E_y = alpha + beta t with a negligible B_z
+    (1e-20) that only serves to make the criterion pick k = 2.  The rotation
+    it causes is ~1e-21, far below FP64 rounding of p_y, so p_y gains exactly
+    q sum_j E(tau_j) h_p(j): Lagrange interpolation of any order >= 1 is exact
+    on a field linear in t, and tau_j is the sub-step's field time."""
+    dt, alpha, beta, bz = 0.5, 0.75, -1.25, 1e-20
+    psi0 = bz * dt / 2.0                     # at rest, gamma = 1
+    prm = oracle.Params(dt=dt, dx=1.0, psi_max=psi0 / 10.0, order=order, field_time=field_time)
+    parts = oracle.Particles([20.25], [0.0], [0.0], [0.0])
+    W_, p = 64, order
+    i0 = np.zeros(2 + p, dtype=np.int64)
+    E = np.array([[alpha + beta * n * dt] * W_ for n in range(-p, 2)])
+    B = np.full((2 + p, W_), bz)
+    st = oracle.run(prm, parts, E, i0, B, i0)
+    return float(parts.py[0]), st
+
+
+def _kicks_closed_form(field_time: int) -> float:
+    """q sum over the two steps of E(tau_j) h_p(j), exact rational arithmetic.
+    Field time (Sec. VI, theta measured from t_n - dt/2 in units of dt):
+    R1 (field_time 0) theta_j = 1/2 + (j-1)/m, R2 (field_time 1) theta_j = (j-1/2)/m.
+    h_p = (h_old + h)/2 on j = 1 (the transitional step, Sec. IV), h after."""
+    dt, alpha, beta = Fraction(1, 2), Fraction(3, 4), Fraction(-5, 4)
+    m = 16
+    h = dt / m
+    total, h_old = Fraction(0), dt
+    for n in (0, 1):
+        for j in range(1, m + 1):
+            theta = Fraction(1, 2) + Fraction(j - 1, m) if field_time == 0 else Fraction(2 * j - 1, 2 * m)
+            tau = n * dt - dt / 2 + theta * dt
+            hp = (h_old + h) / 2 if j == 1 else h
+            total += -(alpha + beta * tau) * hp        # q = -1
+        h_old = h
+    return float(total)
+
+
+@pytest.mark.parametrize("order", [1, 3])
+def test_subcycle_field_time_readings(order):
+    """Both readings of the sub-step field time, pinned by the field they must
+    see: R1 at the position time t_n + (j-1)h, R2 in the middle of the j-th
+    sub-interval of [t_n - dt/2, t_n + dt/2]."""
+    got = {ft: _linear_in_time_kicks(ft, order) for ft in (0, 1)}
+    for ft, (py, st) in got.items():
+        assert st.k_hist[2] == 2 and st.substeps == 32
+        want = _kicks_closed_form(ft)
+        assert abs(py - want) <= 1e-14 * abs(want), (ft, py, want)
+    assert abs(got[0][0] - got[1][0]) > 1e-3          # the two readings differ
+
+
+# ---------------------------------------------------------------- window edge (Eqs. eq:Enp, eq:Bnp)
+
+def test_window_edge_last_valid_node_and_one_past():
+    """The tent gather reads nodes floor(s) and floor(s)+1 of the E grid
+    (s = x/dx) and of the B grid (s - 1/2).  With every level's window on nodes
+    [i0, i0 + W - 1], a particle is pushed iff i0 + 1/2 <= s < i0 + W - 1; one
+    outside that range is frozen (status bit 7) where it stands and counted."""
+    W_, i0v, p = 16, 5, 3
+    lo, hi = i0v + 0.5, float(i0v + W_ - 1)
+    xs = [lo, np.nextafter(lo, -np.inf), hi - 0.25, np.nextafter(hi, -np.inf), hi, hi + 0.5]
+    inside = [True, False, True, True, False, False]
+    prm = oracle.Params(dt=0.5, dx=1.0, psi_max=0.01, order=p)
+    parts = oracle.Particles(xs, [0.0] * 6, [0.0] * 6, [0.0] * 6)
+    i0 = np.full(p + 1, i0v, dtype=np.int64)
+    E = np.zeros((p + 1, W_)); B = np.zeros((p + 1, W_))
+    E[:, -1] = 2.0                    # the last node: a particle that gathers it gets a kick
+    st = oracle.push_step(prm, parts, E, i0, B, i0)
+    lost = (parts.status & 0x80) != 0
+    assert list(~lost) == inside
+    assert st.out_of_window == inside.count(False)
+    np.testing.assert_array_equal(parts.x[lost], np.array(xs)[lost])     # frozen where it stands
+    # the particle in the last cell: tent weight w = s - floor(s) on node W - 1,
+    # q E w (h_old + h)/2 with h_old = h = dt
+    w = (hi - 0.25) - math.floor(hi - 0.25)
+    assert parts.py[2] == -2.0 * w * 0.5
+    assert parts.py[3] == -2.0 * (np.nextafter(hi, -np.inf) - (hi - 1.0)) * 0.5
