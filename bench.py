@@ -60,6 +60,13 @@ def parse():
     ap.add_argument("--batched-steps", type=int, default=200)
     ap.add_argument("--batched-ensembles", type=int, default=512)
     ap.add_argument("--cpu-sample", type=int, default=16384)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-c4", action="store_true")
+    ap.add_argument("--c4-particles", type=int, default=W.C4.n_particles)
+    ap.add_argument("--acc-ulps", default="4",
+                    help="FP32 ulps of the FP64 perturbation runs of the unresolved-front accuracy leg")
+    ap.add_argument("--cpu-threads", type=int, default=0,
+                    help="host threads of the threaded oracle baseline (0: all cores)")
     return ap.parse_args()
 
 
@@ -203,61 +210,6 @@ def levels_np_to_device(wl: W.Workload, n_first: int, n_count: int, device):
     return torch.as_tensor(E, device=device), torch.as_tensor(B, device=device), i0
 
 
-def accuracy_run(wl, ini, n_acc, steps, E, B, i0, ring, stream, dev, sched, sensitivity):
-    """Mixed (binned) vs FP64 (plain) on the first n_acc electrons from step 0.
-    With sensitivity=True a second FP64 run starts from the mixed form's rounded
-    initial state: the spread it shows is the trajectories' own sensitivity."""
-    import torch
-    from paper_2102_10983_gb300 import native
-    p = wl.order
-
-    def run(precision, schedule, init):
-        integ = native.Integrator(wl.dt, wl.dx, wl.psi_max, order=p, precision=precision,
-                                  schedule=schedule, capacity=n_acc, window=wl.window,
-                                  ring_levels=ring, stream=stream)
-        integ.pic_particles_write(*init)
-        for r in range(steps + p):
-            integ.pic_fields_upload(r - p, int(i0[r]), E[r], B[r])
-        integ.pic_push_step(0, steps, want_stats=False)
-        outp = [torch.empty(n_acc, dtype=torch.float64, device=dev) for _ in range(4)]
-        integ.pic_particles_read(*outp)
-        torch.cuda.synchronize()
-        integ.close()
-        return outp
-
-    init = [torch.as_tensor(np.ascontiguousarray(a[:n_acc]), device=dev)
-            for a in (ini.x, ini.px, ini.py, ini.pz)]
-    ref = run(native.PIC_FP64, native.PIC_SCHED_PLAIN, init)
-    mix = run(native.PIC_MIXED, sched, init)
-
-    def cmp(a, b):
-        dpv = torch.stack([(a[q] - b[q]).abs() for q in (1, 2, 3)]).amax(0) / wl.a0 ** 2
-        ga = torch.sqrt(1 + a[1] ** 2 + a[2] ** 2 + a[3] ** 2) - 1
-        gb = torch.sqrt(1 + b[1] ** 2 + b[2] ** 2 + b[3] ** 2) - 1
-        disp = ((a[0] - b[0]).abs() / torch.clamp((a[0] - init[0]).abs(), min=1.0)).max()
-        return {"max_dp_over_a0sq": float(dpv.max()),
-                "frac_dp_over_1e-4": float((dpv > 1e-4).double().mean()),
-                "p99.9_dp_over_a0sq": float(torch.quantile(dpv[:1 << 20].float(), 0.999)),
-                "energy_gain_rel_diff": abs(float(ga.mean() - gb.mean())) / float(ga.mean()),
-                "max_rel_displacement_err": float(disp)}
-
-    res = {"vs": "FP64 GPU form (bit-identical to the FP64 oracle)", "electrons": n_acc,
-           "steps": steps, **cmp(ref, mix)}
-    if sensitivity:
-        # the mixed form's initial rounding, pushed in FP64
-        tmp = native.Integrator(wl.dt, wl.dx, wl.psi_max, order=p, precision=native.PIC_MIXED,
-                                capacity=n_acc, window=wl.window, ring_levels=p + 2, stream=stream)
-        tmp.pic_particles_write(*init)
-        r0 = [torch.empty(n_acc, dtype=torch.float64, device=dev) for _ in range(4)]
-        tmp.pic_particles_read(*r0)
-        torch.cuda.synchronize()
-        tmp.close()
-        ref2 = run(native.PIC_FP64, native.PIC_SCHED_PLAIN, r0)
-        res["fp64_self_sensitivity"] = {
-            "what": "FP64 run from the FP32-rounded initial state vs FP64 run", **cmp(ref, ref2)}
-    return res
-
-
 def batched_workload(n_ens: int, seed: int = 3):
     """512 independent ensembles cycling a0 x resolution x Psi_max over
     {10, 30, 100, 300} x {25, 50, 75, 150} x {0.003, 0.01, 0.03}; sizes
@@ -338,6 +290,66 @@ def run_batched(args, dev, stream):
 
 # ---------------------------------------------------------------- our arm
 
+# FP64 pipe cost of the FP64 form (push_f64_kernel<3>), counted from its source
+# in DFMA issue slots: per Boris sub-step 77 FP64 add/mul/compare/floor
+# operations (two order-3 gathers 34, Boris and position 33, coordinates and
+# window test 10) plus 2 square roots and 3 divisions; per macro step the
+# criterion adds one gather, a square root and a division (27 operations).  A
+# square root or division occupies the pipe ~10 DFMA slots (measured 0.19 of
+# them per clock per SM against 1.92 DFMAs).
+F64_SLOTS_PER_SUBSTEP = 77 + 5 * 10
+F64_SLOTS_PER_STEP = 27 + 2 * 10
+DFMA_PER_CLK_PER_SM = 1.92
+
+
+def device_props(local):
+    import torch
+    pr = torch.cuda.get_device_properties(local)
+    return pr.multi_processor_count
+
+
+def fp64_roofline(st, steps_particles, ms, sms, sm_mhz):
+    """FP64-pipe roofline of the FP64 form: DFMA slots the run needed over the
+    time, against sms x 1.92 x clock."""
+    slots = st["substeps"] * F64_SLOTS_PER_SUBSTEP + steps_particles * F64_SLOTS_PER_STEP
+    achieved = slots / (ms / 1e3)
+    peak = sms * DFMA_PER_CLK_PER_SM * sm_mhz * 1e6
+    return {"bound": "alu (FP64 pipe)", "achieved": achieved, "peak": peak,
+            "unit": "DFMA slots/s", "frac": achieved / peak,
+            "model": f"{F64_SLOTS_PER_SUBSTEP} slots per Boris sub-step + {F64_SLOTS_PER_STEP} per "
+                     "macro step (sqrt/div = 10 slots); peak = SMs x 1.92 DFMA/clk x SM clock"}
+
+
+def snapshot(integ, n_e, dev):
+    """The context's particle state, widened to FP64, on the device."""
+    import torch
+    st0 = [torch.empty(n_e, dtype=torch.float64, device=dev) for _ in range(4)]
+    stat0 = torch.empty(n_e, dtype=torch.uint8, device=dev)
+    integ.pic_particles_read(*st0, stat0)
+    torch.cuda.synchronize()
+    return st0, stat0
+
+
+def timed_call(integ, n0, K, stream, ws):
+    """K macro steps in one call, CUDA events on the launching stream; also the
+    push kernel's own bracketed time per step and the launches queued."""
+    import torch
+    launches0 = integ.launches()
+    integ.timing(True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    integ.pic_push_step(n0, K, want_stats=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = max_over_ranks(ws, ev0.elapsed_time(ev1))
+    kern_ms, kern_steps = integ.timing_read()
+    integ.timing(False)
+    return ms, kern_ms / max(kern_steps, 1), integ.launches() - launches0
+
+
 def run_ours(args, ws, rank, local):
     import torch
     from paper_2102_10983_gb300 import native
@@ -345,6 +357,7 @@ def run_ours(args, ws, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
+    sms = device_props(local)
     wl = rank_workload(rank, args.particles, args.order)
     p = wl.order
     start, Wu, K = args.start_step, args.warmup, args.steps
@@ -357,13 +370,17 @@ def run_ours(args, ws, rank, local):
     E, B, i0 = device_levels(wl, -p, last + p, dev)
     ring = last + p + 1
 
-    def make(precision, schedule, levels_upto):
-        integ = native.Integrator(wl.dt, wl.dx, wl.psi_max, order=p, precision=precision,
-                                  schedule=schedule, capacity=n_e, window=wl.window,
-                                  ring_levels=ring, stream=stream, heavy_budget=args.heavy_budget)
-        integ.pic_particles_write(ini.x, ini.px, ini.py, ini.pz)
+    def make(precision, schedule, levels_upto, state=None, w=wl, Ed=E, Bd=B, io=i0):
+        integ = native.Integrator(w.dt, w.dx, w.psi_max, order=p, precision=precision,
+                                  schedule=schedule, capacity=w.n_particles, window=w.window,
+                                  ring_levels=levels_upto + p + 1, stream=stream,
+                                  heavy_budget=args.heavy_budget)
+        if state is None:
+            integ.pic_particles_write(ini.x, ini.px, ini.py, ini.pz)
+        else:
+            integ.pic_particles_write(*state[0], state[1])
         for r in range(levels_upto + p):
-            integ.pic_fields_upload(r - p, int(i0[r]), E[r], B[r])
+            integ.pic_fields_upload(r - p, int(io[r]), Ed[r], Bd[r])
         return integ
 
     out = {}
@@ -373,53 +390,44 @@ def run_ours(args, ws, rank, local):
         integ.pic_push_step(0, start, want_stats=False)
     integ.pic_push_step(start, Wu, want_stats=False)
     integ.pic_stats_read(reset=True)
-    torch.cuda.synchronize()
+    # the state at the start of the timed window, for the plain and FP64 legs
+    state0 = snapshot(integ, n_e, dev)
     clocks = ClockSampler(local)
     clocks.start()
-    launches0 = integ.launches()
-    integ.timing(True)
-    barrier(ws)
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    integ.pic_push_step(start + Wu, K, want_stats=False)   # one call: K macro steps
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    barrier(ws)
-    total_ms = ev0.elapsed_time(ev1)
-    kern_ms, kern_steps = integ.timing_read()
-    integ.timing(False)
-    launches = integ.launches() - launches0
+    total_ms, kern_ms, launches = timed_call(integ, start + Wu, K, stream, ws)
     clk = clocks.stop()
     st = integ.pic_stats_read(reset=True)
     integ.close()
-    total_ms = max_over_ranks(ws, total_ms)
     ps = aggregate_value(n_e, K, ws, total_ms)
-    substeps = max(st.substeps, 1)
     out.update(value=ps, ms_per_step=total_ms / K, launches=launches, clocks=clk,
-               kern_ms=kern_ms / max(kern_steps, 1), stats=st.as_dict(),
+               kern_ms=kern_ms, stats=st.as_dict(),
                substeps_per_s=st.substeps * ws / (total_ms / 1e3))
+
+    # ---- the plain (unbinned) schedule of the same form on the same window:
+    #      one thread per electron, no binning -- the schedule the others are judged by
+    if not args.no_plain:
+        pl = make(native.PIC_MIXED, native.PIC_SCHED_PLAIN, last, state=state0)
+        torch.cuda.synchronize()
+        ms_pl, kern_pl, la_pl = timed_call(pl, start + Wu, K, stream, ws)
+        st_pl = pl.pic_stats_read(reset=True)
+        pl.close()
+        out["plain"] = {"value": aggregate_value(n_e, K, ws, ms_pl), "ms_per_step": ms_pl / K,
+                        "kern_ms": kern_pl, "gpu_launches": la_pl,
+                        "same_k_hist_as_binned": list(st_pl.k_hist) == list(st.k_hist),
+                        "note": "same form and window, one thread per electron, no binning; "
+                                "started from the binned run's state at the window start"}
 
     # ---- the learned schedule: the predictor trained on pairs the integrator
     #      logs from an at-rest a0 = 100 run, then the same timed window
+    net = None
     if not args.no_learned:
-        out["learned"] = run_learned(args, make, start, Wu, K, last, n_e, ws, stream)
+        out["learned"], net = run_learned(args, make, start, Wu, K, last, n_e, ws, stream)
 
     # ---- the plain FP64 push from the same state (the mixed state at the start of
     #      the timed window, widened to FP64), K64 steps
     K64 = min(K, args.fp64_steps)
     if not args.no_fp64:
-        mix = make(native.PIC_MIXED, sched, last)
-        mix.pic_push_step(0, start + Wu, want_stats=False)
-        st0 = [torch.empty(n_e, dtype=torch.float64, device=dev) for _ in range(4)]
-        stat0 = torch.empty(n_e, dtype=torch.uint8, device=dev)
-        mix.pic_particles_read(*st0, stat0)
-        mix.close()
-        ref = native.Integrator(wl.dt, wl.dx, wl.psi_max, order=p, precision=native.PIC_FP64,
-                                capacity=n_e, window=wl.window, ring_levels=ring, stream=stream)
-        ref.pic_particles_write(*st0, stat0)
-        for r in range(last + p):
-            ref.pic_fields_upload(r - p, int(i0[r]), E[r], B[r])
+        ref = make(native.PIC_FP64, native.PIC_SCHED_PLAIN, last, state=state0)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -427,27 +435,34 @@ def run_ours(args, ws, rank, local):
         e1.record(stream)
         torch.cuda.synchronize()
         ms64 = max_over_ranks(ws, e0.elapsed_time(e1))
+        st64 = ref.pic_stats_read(reset=True).as_dict()
         ref.close()
-        del st0, stat0
+        sm_mhz = clk.get("sm_mhz") or 2070.0
         out.update(fp64_value=n_e * K64 * ws / (ms64 / 1e3), fp64_ms_per_step=ms64 / K64,
-                   fp64_steps=K64)
+                   fp64_steps=K64,
+                   fp64_roofline=fp64_roofline(st64, n_e * K64, ms64, sms, sm_mhz))
+    del state0
 
     # ---- accuracy of the mixed form against the FP64 form (bit-identical to the
     #      FP64 oracle) on the first n_acc electrons, steps 0 .. acc_end-1
     if not args.no_accuracy:
+        from paper_2102_10983_gb300 import accuracy
         n_acc = min(args.acc_particles, n_e)
         acc_end = start + Wu + K64
-        out["accuracy"] = {
-            "switched_on_front": accuracy_run(wl, ini, n_acc, acc_end, E, B, i0, ring, stream,
-                                              dev, sched, sensitivity=True),
-        }
-        smooth = W.Workload(**{**wl.__dict__, "profile": "gauss", "xi0": 8 * math.pi,
+        init = [torch.as_tensor(np.ascontiguousarray(a[:n_acc]), device=dev)
+                for a in (ini.x, ini.px, ini.py, ini.pz)]
+        ulps = tuple(int(u) for u in args.acc_ulps.split(",") if u)
+        sub = W.Workload(**{**wl.__dict__, "n_particles": n_acc})
+        out["accuracy"] = {"switched_on_front": accuracy.front_accuracy(
+            native, sub, init, acc_end, E, B, i0, acc_end + p + 1, stream, sched,
+            unresolved=True, ulps=ulps, heavy_budget=args.heavy_budget)}
+        smooth = W.Workload(**{**sub.__dict__, "profile": "gauss", "xi0": 8 * math.pi,
                                "sigma": 2 * math.pi})
         Es, Bs, _ = levels_np_to_device(smooth, -p, acc_end + p, dev)
-        out["accuracy"]["smooth_front"] = accuracy_run(smooth, ini, n_acc, acc_end, Es, Bs, i0,
-                                                       ring, stream, dev, sched,
-                                                       sensitivity=False)
-        del Es, Bs
+        out["accuracy"]["smooth_front"] = accuracy.front_accuracy(
+            native, smooth, init, acc_end, Es, Bs, i0, acc_end + p + 1, stream, sched,
+            heavy_budget=args.heavy_budget)
+        del Es, Bs, init
 
     # ---- end to end through the C ABI with host buffers
     if not args.no_e2e:
@@ -473,9 +488,86 @@ def run_ours(args, ws, rank, local):
         out["e2e"] = {"value": n_e * Ke * ws / e2e_s, "unit": UNIT, "steps": Ke,
                       "h2d_bytes_per_step": 2 * wl.window * 8,
                       "d2h_bytes_per_step": int(native.ctypes.sizeof(native.PicStepStats))}
+    del E, B
+    if not args.no_c4:
+        out["c4"] = run_c4(args, dev, stream, net, ws)
+    if net is not None:
+        net.close()
     if not args.no_batched:
         out["batched"] = run_batched(args, dev, stream)
     return wl, out
+
+
+def run_c4(args, dev, stream, net, ws):
+    """The learned-binning configuration: 67,108,864 electrons, a0 = 300,
+    Maxwellian 10 keV, Psi_max = 0.01, third order, the timed window with the
+    front in the middle of the cloud; plain, exact-binned and learned schedules
+    from the same state.  The network is the one trained on at-rest a0 = 100
+    pairs (a shift of distribution: thermal electrons, twice the field)."""
+    import torch
+    from paper_2102_10983_gb300 import native
+    wl = W.Workload(**{**W.C4.__dict__, "n_particles": args.c4_particles})
+    p = wl.order
+    start, Wu, K = args.start_step, args.warmup, args.steps
+    last = start + Wu + K
+    n_e = wl.n_particles
+    ini = wl.particles()
+    E, B, i0 = device_levels(wl, -p, last + p, dev)
+
+    def make(schedule, state=None):
+        integ = native.Integrator(wl.dt, wl.dx, wl.psi_max, order=p, precision=native.PIC_MIXED,
+                                  schedule=schedule, capacity=n_e, window=wl.window,
+                                  ring_levels=last + p + 1, stream=stream,
+                                  heavy_budget=args.heavy_budget)
+        if state is None:
+            integ.pic_particles_write(ini.x, ini.px, ini.py, ini.pz)
+        else:
+            integ.pic_particles_write(*state[0], state[1])
+        for r in range(last + p):
+            integ.pic_fields_upload(r - p, int(i0[r]), E[r], B[r])
+        return integ
+
+    res = {"workload": f"{wl.name}: {n_e} electrons, a0 = {wl.a0}, Maxwellian 10 keV, "
+                       f"Psi_max = {wl.psi_max}, order {p}, steps {start + Wu}..{last - 1}"}
+    ex = make(native.PIC_SCHED_BINNED)
+    ex.pic_push_step(0, start + Wu, want_stats=False)
+    ex.pic_stats_read(reset=True)
+    state0 = snapshot(ex, n_e, dev)
+    del ini
+    ms, kern, la = timed_call(ex, start + Wu, K, stream, ws)
+    st = ex.pic_stats_read(reset=True)
+    ex.close()
+    res["exact_binned"] = {"value": aggregate_value(n_e, K, ws, ms), "ms_per_step": ms / K,
+                           "kern_ms": kern, "gpu_launches": la}
+    res["k_hist"] = list(st.k_hist)
+    res["substeps_per_step"] = st.substeps / K
+    if not args.no_plain:
+        pl = make(native.PIC_SCHED_PLAIN, state0)
+        ms, kern, la = timed_call(pl, start + Wu, K, stream, ws)
+        st_pl = pl.pic_stats_read(reset=True)
+        pl.close()
+        res["plain"] = {"value": aggregate_value(n_e, K, ws, ms), "ms_per_step": ms / K,
+                        "kern_ms": kern, "gpu_launches": la,
+                        "same_k_hist": list(st_pl.k_hist) == list(st.k_hist)}
+    if net is not None:
+        le = make(native.PIC_SCHED_PREDICTED, state0)
+        le.attach_predictor(net, args.predict_every)
+        pred0 = torch.empty(n_e, dtype=torch.uint8, device=dev)
+        native.predict(le, net, start + Wu - 1, pred0)
+        res["predicted_k_hist_first_step"] = torch.bincount(pred0.long(), minlength=8).tolist()
+        del pred0
+        torch.cuda.synchronize()
+        ms, kern, la = timed_call(le, start + Wu, K, stream, ws)
+        st_le = le.pic_stats_read(reset=True)
+        le.close()
+        res["learned"] = {"value": aggregate_value(n_e, K, ws, ms), "ms_per_step": ms / K,
+                          "kern_ms": kern, "gpu_launches": la, "predict_every": args.predict_every,
+                          "same_k_hist": list(st_le.k_hist) == list(st.k_hist)}
+    res["note"] = ("state of the exact-binned run at the window start copied to the plain and "
+                   "learned runs; the criterion's k_hist is over the timed steps")
+    del state0, E, B
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_learned(args, make, start, Wu, K, last, n_e, ws, stream):
@@ -505,56 +597,53 @@ def run_learned(args, make, start, Wu, K, last, n_e, ws, stream):
     pred_hist = torch.bincount(pred0.long(), minlength=8).tolist()
     del pred0
     torch.cuda.synchronize()
-    integ.timing(True)
-    launches0 = integ.launches()
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
-    barrier(ws)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    integ.pic_push_step(start + Wu, K, want_stats=False)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(ws)
+    ms, kern_ms, launches = timed_call(integ, start + Wu, K, stream, ws)
     clk = clocks.stop()
-    ms = max_over_ranks(ws, e0.elapsed_time(e1))
-    launches = integ.launches() - launches0
-    kern_ms, kern_steps = integ.timing_read()
     integ.close()
-    net.close()
-    return {"value": aggregate_value(n_e, K, ws, ms), "ms_per_step": ms / K,
-            "kern_ms": kern_ms / max(kern_steps, 1), "clocks": clk,
-            "predict_every": args.predict_every, "gpu_launches": launches,
-            "predicted_k_hist_first_step": pred_hist,
-            "training": {"pairs": int(len(Y)), "held_out_accuracy": acc,
-                         "same_k_as_last_step_accuracy": acc_prev,
-                         "k_ge_3_recall": heavy_recall, "k_ge_3_false_alarm_rate": false_alarm,
-                         "loss_first_last": [losses[0], losses[-1]], "seconds": train_s,
-                         "data": "features after step n and k of step n+1, logged by the integrator "
-                                 "on 65,536 at-rest electrons in a0 = 100, lambda/75, 400 steps "
-                                 "(every pair kept: natural class frequencies)"}}
+    return ({"value": aggregate_value(n_e, K, ws, ms), "ms_per_step": ms / K,
+             "kern_ms": kern_ms, "clocks": clk,
+             "predict_every": args.predict_every, "gpu_launches": launches,
+             "predicted_k_hist_first_step": pred_hist,
+             "training": {"pairs": int(len(Y)), "held_out_accuracy": acc,
+                          "same_k_as_last_step_accuracy": acc_prev,
+                          "k_ge_3_recall": heavy_recall, "k_ge_3_false_alarm_rate": false_alarm,
+                          "loss_first_last": [losses[0], losses[-1]], "seconds": train_s,
+                          "data": "features after step n and k of step n+1, logged by the "
+                                  "integrator on 65,536 at-rest electrons in a0 = 100, lambda/75, "
+                                  "400 steps (every pair kept: natural class frequencies)"}},
+            net)
 
 
-def cpu_baseline(wl: W.Workload, n_sample: int, steps: int):
-    """The oracle, as it stands, on one host core: the first n_sample electrons
-    of the workload through its first `steps` macro steps."""
+def cpu_baseline(wl: W.Workload, n_sample: int, steps: int, threads: int = 1):
+    """The oracle, as it stands, on `threads` host cores: the first n_sample
+    electrons of the workload through its first `steps` macro steps, dealt
+    round-robin into one particle set per thread (equal work: the electrons are
+    stored by initial position, so the front reaches a contiguous range all at
+    once); the oracle's library call releases the interpreter lock, so the sets
+    run in parallel."""
     import oracle
+    from concurrent.futures import ThreadPoolExecutor
     p = wl.order
     prm = oracle.Params(dt=wl.dt, dx=wl.dx, psi_max=wl.psi_max, order=p)
     ini = wl.particles(n_sample)
-    parts = oracle.Particles(ini.x, ini.px, ini.py, ini.pz)
+    parts = [oracle.Particles(ini.x[q::threads], ini.px[q::threads], ini.py[q::threads],
+                              ini.pz[q::threads]) for q in range(threads)]
+    stats = [oracle.OrcStats() for _ in parts]
     oracle.lib()
     t_cpu = 0.0
     done = 0
-    st = oracle.OrcStats()
-    while done < steps:
-        c = min(500, steps - done)
-        E, B, i0 = wl.levels(done - p, c + p)
-        t0 = time.perf_counter()
-        oracle.run(prm, parts, E, i0, B, i0, st)
-        t_cpu += time.perf_counter() - t0
-        done += c
-    return n_sample * steps / t_cpu, st
+    with ThreadPoolExecutor(max_workers=threads) as pool:
+        while done < steps:
+            c = min(500, steps - done)
+            E, B, i0 = wl.levels(done - p, c + p)
+            t0 = time.perf_counter()
+            list(pool.map(lambda q: oracle.run(prm, parts[q], E, i0, B, i0, stats[q]),
+                          range(len(parts))))
+            t_cpu += time.perf_counter() - t0
+            done += c
+    return n_sample * steps / t_cpu, stats
 
 
 def run_reference(args, ws, rank):
@@ -637,9 +726,11 @@ def main():
         "substeps_per_s": out["substeps_per_s"],
         "exact_binned": {"value": out["value"], "ms_per_step": out["ms_per_step"],
                          "note": "same form, electrons binned by the exact criterion only"},
+        "plain": out.get("plain"),
         "learned": out.get("learned"),
         "fp64_value": out.get("fp64_value"), "fp64_steps": out.get("fp64_steps"),
         "fp64_note": "plain FP64 push, same workload and steps, started from the timed window's state",
+        "fp64_roofline": out.get("fp64_roofline"),
         "speedup_vs_fp64": (headline["value"] / out["fp64_value"]) if out.get("fp64_value") else None,
         "accuracy": out.get("accuracy"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -655,13 +746,26 @@ def main():
     }
     if "e2e" in out:
         line["e2e"] = out["e2e"]
+    if "c4" in out:
+        line["c4"] = out["c4"]
     if "batched" in out:
-        line["batched"] = out["batched"]
+        b = out["batched"]
+        ach = bytes_per * b["electrons"] / (b["ms_per_step"] / 1e3) / 1e9
+        b["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                         "frac": ach / hbm, "note": "42 B per electron-step over the whole step "
+                                                   "(push and per-step field kernels)"}
+        line["batched"] = b
     if not args.no_cpu_baseline:
-        v, _ = cpu_baseline(wl, args.cpu_sample, 1000)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"first {args.cpu_sample} electrons x steps 0..999 "
-                                          f"of the same workload, serial FP64"}
+        threads = args.cpu_threads or os.cpu_count() or 1
+        v1, _ = cpu_baseline(wl, args.cpu_sample, 1000)
+        vt, _ = cpu_baseline(wl, args.cpu_sample * threads, 1000, threads)
+        line["cpu_baseline"] = {"value": vt, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": f"first {args.cpu_sample * threads} electrons x steps "
+                                          f"0..999 of the same workload, FP64, {threads} threads "
+                                          f"(electrons dealt round-robin)",
+                                "serial": {"value": v1, "cores": 1,
+                                           "sample": f"first {args.cpu_sample} electrons x steps "
+                                                     "0..999, one thread"}}
     print(json.dumps(line))
 
 

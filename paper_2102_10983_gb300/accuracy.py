@@ -1,0 +1,151 @@
+"""Accuracy of the mixed-precision push against the FP64 push, on the device.
+
+Measurement code shared by the benchmark and the GPU tests: it runs the C-ABI
+integrator in both forms over the same levels and compares the final states.
+No integrator arithmetic lives here.
+
+Metrics (per electron, then over the ensemble), against an FP64 reference:
+  dp   = max over components |p - p_ref| / a0^2           (max, fraction > 1e-4,
+                                                            99.9th percentile)
+  energy gain: | <gamma - 1> - <gamma_ref - 1> | / <gamma_ref - 1>
+  displacement: max |x - x_ref| / max(|x_ref - x0|, 1)
+
+Unresolved fronts.  Where the wave is switched on with a jump no grid
+resolves, the FP64 method itself is hypersensitive: an initial state perturbed
+by a few FP32 units in the last place already moves a fraction of the electrons
+past dp = 1e-4.  There the mixed form is held to a backward-error bound: its
+error (against the FP64 form started from the same, FP32-rounded, state) may be
+no worse than the FP64 form's own response to a perturbation of the initial
+state by `ulps` FP32 units in the last place (positions by ulps * 2^-24 cells,
+momenta by a factor 1 + ulps * 2^-24, signs from a fixed seed).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+U32 = 2.0 ** -24   # FP32 unit roundoff: half an ulp at 1
+
+
+def compare(a, b, x0, a0):
+    """Metrics of state a (x, px, py, pz tensors) against reference b."""
+    import torch
+    dpv = torch.stack([(a[q] - b[q]).abs() for q in (1, 2, 3)]).amax(0) / a0 ** 2
+    ga = torch.sqrt(1 + a[1] ** 2 + a[2] ** 2 + a[3] ** 2) - 1
+    gb = torch.sqrt(1 + b[1] ** 2 + b[2] ** 2 + b[3] ** 2) - 1
+    disp = ((a[0] - b[0]).abs() / torch.clamp((b[0] - x0).abs(), min=1.0)).max()
+    sample = dpv[: 1 << 20].float()
+    return {"max_dp_over_a0sq": float(dpv.max()),
+            "frac_dp_over_1e-4": float((dpv > 1e-4).double().mean()),
+            "p99.9_dp_over_a0sq": float(torch.quantile(sample, 0.999)),
+            "energy_gain_rel_diff": abs(float(ga.mean() - gb.mean())) / float(gb.mean()),
+            "max_rel_displacement_err": float(disp)}
+
+
+def perturbed(init, dx, ulps, seed=11):
+    """The initial state moved by `ulps` FP32 units: x by +-ulps 2^-24 dx,
+    each momentum component by a factor 1 +- ulps 2^-24."""
+    import torch
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    out = []
+    for q, a in enumerate(init):
+        s = (torch.randint(0, 2, a.shape, generator=g, dtype=torch.int8) * 2 - 1).to(
+            device=a.device, dtype=a.dtype)
+        if q == 0:
+            out.append(a + s * (ulps * U32 * dx))
+        else:
+            out.append(a * (1 + s * (ulps * U32)))
+    return out
+
+
+def run_form(native, wl, precision, schedule, init, steps, E, B, i0, ring, stream, heavy_budget=0):
+    """Steps 0 .. steps-1 of workload wl from state init (device FP64 tensors),
+    levels E, B (device, rows = levels -p ..) in one call; returns the final state."""
+    import torch
+    p = wl.order
+    n = int(init[0].shape[0])
+    integ = native.Integrator(wl.dt, wl.dx, wl.psi_max, order=p, precision=precision,
+                              schedule=schedule, capacity=n, window=wl.window,
+                              ring_levels=ring, stream=stream, heavy_budget=heavy_budget)
+    integ.pic_particles_write(*init)
+    for r in range(steps + p):
+        integ.pic_fields_upload(r - p, int(i0[r]), E[r], B[r])
+    integ.pic_push_step(0, steps, want_stats=False)
+    out = [torch.empty(n, dtype=torch.float64, device=init[0].device) for _ in range(4)]
+    integ.pic_particles_read(*out)
+    torch.cuda.synchronize()
+    integ.close()
+    return out
+
+
+def rounded_start(native, wl, init, stream):
+    """The mixed form's own initial state (cell + FP32 offset, FP32 momenta),
+    widened back to FP64."""
+    import torch
+    n = int(init[0].shape[0])
+    tmp = native.Integrator(wl.dt, wl.dx, wl.psi_max, order=wl.order, precision=native.PIC_MIXED,
+                            capacity=n, window=wl.window, ring_levels=wl.order + 2, stream=stream)
+    tmp.pic_particles_write(*init)
+    r0 = [torch.empty(n, dtype=torch.float64, device=init[0].device) for _ in range(4)]
+    tmp.pic_particles_read(*r0)
+    torch.cuda.synchronize()
+    tmp.close()
+    return r0
+
+
+def front_accuracy(native, wl, init, steps, E, B, i0, ring, stream, schedule,
+                   unresolved=False, ulps=(1, 4, 16), heavy_budget=0):
+    """The mixed form (schedule) against the FP64 form on one front.
+
+    Always: mixed vs FP64 from the same FP64 start ("vs_fp64").  With
+    unresolved=True also: FP64 from the mixed form's rounded start (the
+    reference of the mixed arithmetic alone, "mixed_vs_fp64_same_start"), the
+    FP64 form's spread under that rounding ("fp64_self_sensitivity") and under
+    perturbations of `ulps` FP32 units ("fp64_perturbed_<u>ulp")."""
+    ref = run_form(native, wl, native.PIC_FP64, native.PIC_SCHED_PLAIN, init, steps, E, B, i0,
+                   ring, stream)
+    mix = run_form(native, wl, native.PIC_MIXED, schedule, init, steps, E, B, i0, ring, stream,
+                   heavy_budget)
+    res = {"vs": "FP64 GPU form (bit-identical to the FP64 oracle)", "electrons": int(init[0].shape[0]),
+           "steps": steps, **compare(mix, ref, init[0], wl.a0)}
+    if unresolved:
+        r0 = rounded_start(native, wl, init, stream)
+        ref_r = run_form(native, wl, native.PIC_FP64, native.PIC_SCHED_PLAIN, r0, steps, E, B, i0,
+                         ring, stream)
+        res["mixed_vs_fp64_same_start"] = compare(mix, ref_r, init[0], wl.a0)
+        res["fp64_self_sensitivity"] = {
+            "what": "FP64 run from the FP32-rounded initial state vs FP64 run",
+            **compare(ref_r, ref, init[0], wl.a0)}
+        for u in ulps:
+            ref_u = run_form(native, wl, native.PIC_FP64, native.PIC_SCHED_PLAIN,
+                             perturbed(init, wl.dx, u), steps, E, B, i0, ring, stream)
+            res[f"fp64_perturbed_{u}ulp"] = compare(ref_u, ref, init[0], wl.a0)
+    return res
+
+
+# FP32 ulps of the initial-state perturbation whose effect on the FP64 form
+# bounds the mixed form's error on an unresolved front.
+BACKWARD_ULPS = 4
+
+
+def backward_error_ok(res, ulps=BACKWARD_ULPS):
+    """The unresolved-front criterion on a front_accuracy(unresolved=True)
+    result: the mixed form, against the FP64 form from the same rounded start,
+    puts no more electrons past dp = 1e-4 than the FP64 form perturbed by `ulps`
+    FP32 ulps does (with a Poisson allowance of 3 sigma + 3 electrons for small
+    ensembles), its 99.9th percentile of dp is no larger when the ensemble has
+    at least 10^5 electrons, and the energy gains agree to 0.1 %.
+    Returns (ok, reason)."""
+    n = res["electrons"]
+    mix = res["mixed_vs_fp64_same_start"]
+    pert = res[f"fp64_perturbed_{ulps}ulp"]
+    n_mix = mix["frac_dp_over_1e-4"] * n
+    n_pert = pert["frac_dp_over_1e-4"] * n
+    allowance = n_pert + 3.0 * n_pert ** 0.5 + 3.0
+    if n_mix > allowance:
+        return False, f"{n_mix:.0f} electrons past 1e-4 > {allowance:.1f} ({ulps}-ulp FP64 spread)"
+    if n >= 100_000 and mix["p99.9_dp_over_a0sq"] > pert["p99.9_dp_over_a0sq"]:
+        return False, (f"p99.9 {mix['p99.9_dp_over_a0sq']:.3e} > {pert['p99.9_dp_over_a0sq']:.3e} "
+                       f"({ulps}-ulp FP64 spread)")
+    if res["energy_gain_rel_diff"] > 1e-3:
+        return False, f"energy gain differs by {res['energy_gain_rel_diff']:.2e}"
+    return True, "ok"

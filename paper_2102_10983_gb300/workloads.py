@@ -190,3 +190,8 @@ C2 = Workload(name="c2_maxwellian_a0_150_16M", n_particles=16_777_216, a0=150.0,
               dx=DT75 / 0.99, psi_max=0.01, order=3, n_steps=20_000,
               x_lo=0.0, x_hi=64 * TWO_PI, thermal_sigma=MAXWELL_10KEV_SIGMA, seed=2,
               window=32768, window_origin=-512, sort_x=True)
+
+C4 = Workload(name="c4_maxwellian_a0_300_64M", n_particles=67_108_864, a0=300.0, dt=DT75,
+              dx=DT75 / 0.99, psi_max=0.01, order=3, n_steps=10_000,
+              x_lo=0.0, x_hi=64 * TWO_PI, thermal_sigma=MAXWELL_10KEV_SIGMA, seed=4,
+              window=32768, window_origin=-512, sort_x=True)
