@@ -50,7 +50,27 @@ class PicStepStats(ctypes.Structure):
                 "clamped": self.clamped, "out_of_window": self.out_of_window, "error": self.error}
 
 
-# (name, restype, argtypes) of every symbol declared in include/pic_gb300.h
+class PicSc1dParams(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("dx", ctypes.c_double), ("psi_max", ctypes.c_double),
+                ("qm", ctypes.c_double), ("order", ctypes.c_int32), ("k_max", ctypes.c_int32),
+                ("field_time", ctypes.c_int32), ("n_cells", ctypes.c_int32),
+                ("gauss_every", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class PicSc1dStats(ctypes.Structure):
+    _fields_ = [("k_hist", ctypes.c_int64 * 8), ("substeps", ctypes.c_int64),
+                ("n_star", ctypes.c_int64), ("clamped", ctypes.c_int64), ("frozen", ctypes.c_int64),
+                ("gauss_residual", ctypes.c_double), ("rho_max", ctypes.c_double),
+                ("checks", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {"k_hist": list(self.k_hist), "substeps": self.substeps, "n_star": self.n_star,
+                "clamped": self.clamped, "frozen": self.frozen,
+                "gauss_residual": self.gauss_residual, "rho_max": self.rho_max,
+                "checks": self.checks}
+
+
+# (name, restype, argtypes) of every symbol declared in include/*.h
 _VP, _I32, _I64, _D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
 SIGNATURES = {
     "pic_create": (ctypes.c_int, [ctypes.POINTER(PicParams), _I64, _I64, _I32, _VP,
@@ -93,6 +113,17 @@ SIGNATURES = {
     "pic_push_mixed_noalloc": (ctypes.c_int, [ctypes.POINTER(PicParams), _I64, _VP, _VP, _VP, _VP,
                                               _VP, _VP, _VP, _VP, _VP, _I64, _I64, _I64, _VP,
                                               ctypes.POINTER(PicStepStats)]),
+    "pic_sc1d_create": (ctypes.c_int, [ctypes.POINTER(PicSc1dParams), _I64, _VP,
+                                       ctypes.POINTER(_VP)]),
+    "pic_sc1d_destroy": (ctypes.c_int, [_VP]),
+    "pic_sc1d_particles_write": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _I64, _I32]),
+    "pic_sc1d_particles_read": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _I64, _I32]),
+    "pic_sc1d_fields_write": (ctypes.c_int, [_VP, _I64, _VP, _VP, _VP, _I32]),
+    "pic_sc1d_fields_read": (ctypes.c_int, [_VP, _I64, _VP, _VP, _VP, _I32]),
+    "pic_sc1d_step": (ctypes.c_int, [_VP, _I64, _I64, ctypes.POINTER(PicSc1dStats)]),
+    "pic_sc1d_timing": (ctypes.c_int, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
+    "pic_sc1d_launch_count": (ctypes.c_int64, [_VP]),
+    "pic_sc1d_last_error": (ctypes.c_char_p, [_VP]),
 }
 
 _lib = None
@@ -403,3 +434,85 @@ class Batch:
         self._chk(lib().pic_batch_autotune(self.h, int(n), int(steps), ctypes.byref(c),
                                            ctypes.byref(b), ctypes.byref(ms)))
         return c.value, b.value, ms.value
+
+
+class Sc1d:
+    """The self-consistent 1D3V PIC loop of the C library (pic_sc1d_*)."""
+
+    def __init__(self, dt, dx, n_cells, psi_max=0.01, order=3, k_max=7, field_time=0, qm=-1.0,
+                 capacity=0, gauss_every=0, stream=None):
+        self.params = PicSc1dParams(float(dt), float(dx), float(psi_max), float(qm), int(order),
+                                    int(k_max), int(field_time), int(n_cells), int(gauss_every))
+        self.n_cells = int(n_cells)
+        self.M = self.n_cells + 5
+        h = ctypes.c_void_p()
+        self._chk(lib().pic_sc1d_create(ctypes.byref(self.params), int(capacity),
+                                        _stream_handle(stream), ctypes.byref(h)), None)
+        self.h = h
+        self.n = 0
+
+    def _chk(self, code, h="self", ok=(PIC_OK,)):
+        if code not in ok:
+            hh = self.h if h == "self" else h
+            raise PicError(code, (lib().pic_sc1d_last_error(hh) or b"").decode())
+        return code
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pic_sc1d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def particles_write(self, x, px, py, pz, w):
+        n = int(x.shape[0])
+        wh = _where(x, px, py, pz, w)
+        self._chk(lib().pic_sc1d_particles_write(self.h, _ptr(x)[0], _ptr(px)[0], _ptr(py)[0],
+                                                 _ptr(pz)[0], _ptr(w)[0], n, wh))
+        self.n = n
+
+    def particles_read(self, x=None, px=None, py=None, pz=None, status=None, n=None):
+        arrs = [a for a in (x, px, py, pz, status) if a is not None]
+        wh = _where(*arrs)
+        self._chk(lib().pic_sc1d_particles_read(self.h, _ptr(x)[0], _ptr(px)[0], _ptr(py)[0],
+                                                _ptr(pz)[0], _ptr(status)[0],
+                                                self.n if n is None else int(n), wh))
+
+    def fields_write(self, level, Ex, Ey, Bz):
+        wh = _where(Ex, Ey, Bz)
+        assert Ex.shape[-1] == self.M and Ey.shape[-1] == self.M and Bz.shape[-1] == self.M
+        self._chk(lib().pic_sc1d_fields_write(self.h, int(level), _ptr(Ex)[0], _ptr(Ey)[0],
+                                              _ptr(Bz)[0], wh))
+
+    def fields_read(self, level, Ex, Ey, Bz):
+        wh = _where(Ex, Ey, Bz)
+        self._chk(lib().pic_sc1d_fields_read(self.h, int(level), _ptr(Ex)[0], _ptr(Ey)[0],
+                                             _ptr(Bz)[0], wh))
+
+    def step(self, n0, n_steps=1, want_stats=True, ok=(PIC_OK, PIC_EKMAX)):
+        st = PicSc1dStats() if want_stats else None
+        self._chk(lib().pic_sc1d_step(self.h, int(n0), int(n_steps),
+                                      ctypes.byref(st) if st is not None else None), ok=ok)
+        return st
+
+    def timing(self):
+        ms, steps = ctypes.c_double(), ctypes.c_int64()
+        self._chk(lib().pic_sc1d_timing(self.h, ctypes.byref(ms), ctypes.byref(steps)))
+        return ms.value, steps.value
+
+    def launches(self) -> int:
+        return int(lib().pic_sc1d_launch_count(self.h))
+
+    def read_numpy(self):
+        out = [np.empty(self.n) for _ in range(4)] + [np.empty(self.n, np.uint8)]
+        self.particles_read(*out)
+        return out
+
+    def fields_numpy(self, level):
+        out = [np.empty(self.M) for _ in range(3)]
+        self.fields_read(level, *out)
+        return out

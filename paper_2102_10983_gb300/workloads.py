@@ -195,3 +195,121 @@ C4 = Workload(name="c4_maxwellian_a0_300_64M", n_particles=67_108_864, a0=300.0,
               dx=DT75 / 0.99, psi_max=0.01, order=3, n_steps=10_000,
               x_lo=0.0, x_hi=64 * TWO_PI, thermal_sigma=MAXWELL_10KEV_SIGMA, seed=4,
               window=32768, window_origin=-512, sort_x=True)
+
+
+# ---------------------------------------------------------------- self-consistent 1D3V PIC
+
+def sin2_duration_for_fwhm(fwhm: float) -> float:
+    """Total length T of a sin^2(pi xi / T) field envelope whose intensity
+    (sin^4) has the full width at half maximum `fwhm`."""
+    alpha = math.asin(2.0 ** -0.25)
+    return fwhm / (1.0 - 2.0 * alpha / math.pi)
+
+
+@dataclass(frozen=True)
+class LaserPlasma1D:
+    """A laser pulse in vacuum heading into a plasma with an exponential ramp,
+    on a 1D grid of n_cells cells (normalized units, lambda = 2 pi).
+
+    Laser: a = a0 sin^2(pi xi / T) sin(xi) for 0 <= xi <= T, xi = t - x + x_front
+    (front at x_front at t = 0), E_y = B_z = -da/dxi (Eq. laser5); T from the
+    intensity FWHM (fwhm, normalized time).
+    Plasma (electrons; ions an immobile neutralizing background): density
+    n_top exp((x - x_top)/L) on [x_top - ramp_lengths L, x_top), n_top beyond
+    x_top up to the end of the grid minus `tail_gap` cells; ppc electrons per
+    cell on a regular lattice ((c + (j + 1/2)/ppc) dx), at rest, each of weight
+    n(x)/ppc (units of n_c).
+    Grids: E_y on nodes k dx, B_z and E_x on faces (k + 1/2) dx; arrays hold
+    n_cells + 5 entries, index = node (or face) + 2."""
+    name: str
+    n_cells: int
+    a0: float
+    fwhm: float
+    x_front: float
+    x_top: float
+    scale_length: float
+    n_top: float
+    ppc: int
+    dt: float = DT75
+    dx: float = DT75 / 0.99
+    ramp_lengths: float = 6.0
+    gap: float = TWO_PI             # vacuum between the pulse front and the plasma
+    tail_gap: int = 8
+    psi_max: float = 0.01
+    order: int = 3
+
+    @property
+    def duration(self) -> float:
+        return sin2_duration_for_fwhm(self.fwhm)
+
+    def a(self, xi):
+        xi = np.asarray(xi, dtype=np.float64)
+        T = self.duration
+        inside = (xi >= 0.0) & (xi <= T)
+        return np.where(inside, self.a0 * np.sin(math.pi * xi / T) ** 2 * np.sin(xi), 0.0)
+
+    def field(self, xi):
+        """-da/dxi."""
+        xi = np.asarray(xi, dtype=np.float64)
+        T = self.duration
+        inside = (xi >= 0.0) & (xi <= T)
+        env = np.sin(math.pi * xi / T)
+        d = self.a0 * (2.0 * math.pi / T * env * np.cos(math.pi * xi / T) * np.sin(xi)
+                       + env * env * np.cos(xi))
+        return np.where(inside, -d, 0.0)
+
+    def density(self, x):
+        x = np.asarray(x, dtype=np.float64)
+        L = self.scale_length
+        start = self.x_top - self.ramp_lengths * L
+        end = (self.n_cells - self.tail_gap) * self.dx
+        n = np.where(x < self.x_top, self.n_top * np.exp((x - self.x_top) / L), self.n_top)
+        return np.where((x >= start) & (x < end), n, 0.0)
+
+    def particles(self):
+        """(x, px, py, pz, w) of every macro-electron, in order of position."""
+        L = self.scale_length
+        start = self.x_top - self.ramp_lengths * L
+        end = (self.n_cells - self.tail_gap) * self.dx
+        c0 = int(math.ceil(start / self.dx))
+        c1 = int(math.floor(end / self.dx))
+        cells = np.arange(c0, c1, dtype=np.float64)
+        j = (np.arange(self.ppc, dtype=np.float64) + 0.5) / self.ppc
+        x = ((cells[:, None] + j[None, :]) * self.dx).ravel()
+        w = self.density(x) / self.ppc
+        keep = w > 0.0
+        x, w = x[keep], w[keep]
+        z = np.zeros_like(x)
+        return x, z.copy(), z.copy(), z.copy(), w
+
+    def field_history(self):
+        """Levels -p .. 0 of (E_x, E_y) and -p+1/2 .. 1/2 of B_z: the vacuum
+        pulse (E_x = 0: the plasma is neutral and at rest before t = 0)."""
+        p, N = self.order, self.n_cells
+        M = N + 5
+        nodes = np.arange(N + 1, dtype=np.float64)
+        faces = np.arange(N, dtype=np.float64) + 0.5
+        E_hist, B_hist = [], []
+        for lev in range(-p, 1):
+            ey = np.zeros(M)
+            ey[2:N + 3] = self.field(lev * self.dt - nodes * self.dx + self.x_front)
+            E_hist.append((np.zeros(M), ey))
+            bz = np.zeros(M)
+            bz[2:N + 2] = self.field((lev + 0.5) * self.dt - faces * self.dx + self.x_front)
+            B_hist.append(bz)
+        return E_hist, B_hist
+
+
+def laser_plasma_c5(n_cells: int = 20_000, ppc: int = 100, a0: float = 150.0) -> LaserPlasma1D:
+    """The self-consistent configuration: a0 = 150, 30 fs intensity FWHM at
+    820 nm, exponential preplasma (5 lambda scale length) rising to 0.5 n_c,
+    100 electrons per cell, 20,000 cells, c dt/dx = 0.99, dt = lambda/75."""
+    omega = TWO_PI * 299_792_458.0 / 820e-9
+    fwhm = 30e-15 * omega
+    T = sin2_duration_for_fwhm(fwhm)
+    x_front = TWO_PI + T                  # the tail one wavelength from the left edge
+    L = 5 * TWO_PI
+    x_top = x_front + TWO_PI + 6.0 * L    # ramp from n_top e^-6, a wavelength past the front
+    return LaserPlasma1D(name=f"c5_laser_plasma_a0_{a0:g}_{n_cells}cells_{ppc}ppc", n_cells=n_cells,
+                         a0=a0, fwhm=fwhm, x_front=x_front, x_top=x_top, scale_length=L,
+                         n_top=0.5, ppc=ppc)

@@ -33,7 +33,7 @@ def test_device_error_word_is_reported_as_timeout(precision, schedule):
     p = wl.order
     integ = native.Integrator(wl.dt, wl.dx, wl.psi_max, order=p, precision=precision,
                               schedule=schedule, capacity=wl.n_particles, window=wl.window,
-                              ring_levels=p + 2)
+                              ring_levels=p + 4)
     ini = wl.particles()
     integ.pic_particles_write(ini.x, ini.px, ini.py, ini.pz)
     E, B, i0 = wl.levels(-p, p + 3)
