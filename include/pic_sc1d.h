@@ -18,7 +18,8 @@
  *   3. fields: the Yee scheme of Eqs. eq:Ey, eq:Bz with the current J_y,
  *      dE_x/dt = -J_x, first-order Mur boundaries for E_y at both ends.
  * Gauss's law div E_x = rho (immobile ions neutralizing the initial
- * electrons) is checked on the device on request.
+ * electrons) is checked on the device on request; the check keeps running
+ * maxima on the device, so it adds no synchronization.
  *
  * Units and grid: omega = c = m = |e| = 1, densities in n_c.  N cells; E_y on
  * nodes k dx (time levels n dt), E_x on faces (k + 1/2) dx (levels n dt), B_z
@@ -64,7 +65,7 @@ typedef struct {
   int64_t clamped;         /* macro steps whose k was capped at k_max              */
   int64_t frozen;          /* electrons frozen (left the interior)                 */
   double gauss_residual;   /* max over the checks of max_k |div E_x - rho|_k        */
-  double rho_max;          /* max_k |rho_e| at the last check                      */
+  double rho_max;          /* max over the checks of max_k |rho_e|_k                */
   int32_t checks;          /* Gauss checks made                                     */
   int32_t reserved;
 } pic_sc1d_stats;
@@ -101,8 +102,9 @@ int pic_sc1d_fields_read(pic_sc1d* c, int64_t level, double* Ex, double* Ey, dou
                          int32_t where);
 
 /* Macro steps n0 .. n0 + n_steps - 1 (push, deposit, field solve; Gauss check
- * every gauss_every steps).  Level n0 must be the newest stored.  With stats:
- * synchronizes, returns and resets the counters (PIC_EKMAX if k was capped).
+ * after every gauss_every-th step of the call).  Level n0 must be the newest
+ * stored.  With stats: synchronizes, returns and resets the counters and the
+ * Gauss maxima accumulated since the last stats (PIC_EKMAX if k was capped).
  * Errors: PIC_EINVAL, PIC_ECUDA, PIC_EKMAX. */
 int pic_sc1d_step(pic_sc1d* c, int64_t n0, int64_t n_steps, pic_sc1d_stats* stats);
 

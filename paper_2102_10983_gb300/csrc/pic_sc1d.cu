@@ -509,7 +509,6 @@ extern "C" int pic_sc1d_fields_read(pic_sc1d* c, int64_t level, double* Ex, doub
 
 static int sc_gauss(pic_sc1d* c) {
   SC_TRY(c, cudaMemsetAsync(accC(c), 0, c->M * 8, c->stream));
-  SC_TRY(c, cudaMemsetAsync(accGauss(c), 0, 16, c->stream));
   if (c->n > 0) {
     rho_kernel<<<grid_for(c, c->n), 256, 0, c->stream>>>(c->x, c->Q, c->n, 1.0 / c->prm.dx, accC(c), c->M, 0);
     ++c->launches;
@@ -597,15 +596,7 @@ extern "C" int pic_sc1d_step(pic_sc1d* c, int64_t n0, int64_t n_steps, pic_sc1d_
                                                              c->prm.n_cells, 1.0 / c->prm.dx,
                                                              accGauss(c));
       ++c->launches;
-      unsigned long long g[2];
-      SC_TRY(c, cudaMemcpyAsync(g, accGauss(c), 16, cudaMemcpyDeviceToHost, c->stream));
-      SC_TRY(c, cudaStreamSynchronize(c->stream));
-      double gv, rv;
-      memcpy(&gv, &g[0], 8);
-      memcpy(&rv, &g[1], 8);
-      if (gv > c->gauss_res) c->gauss_res = gv;
-      c->rho_max = rv;
-      ++c->checks;
+      ++c->checks;  // the maxima accumulate on the device until stats are read
     }
   }
   if (c->timing) {
@@ -618,9 +609,14 @@ extern "C" int pic_sc1d_step(pic_sc1d* c, int64_t n0, int64_t n_steps, pic_sc1d_
   }
   if (!stats) return PIC_OK;
   DevStats h;
+  unsigned long long g[2];
   SC_TRY(c, cudaMemcpyAsync(&h, c->dstats, sizeof(DevStats), cudaMemcpyDeviceToHost, c->stream));
+  SC_TRY(c, cudaMemcpyAsync(g, accGauss(c), 16, cudaMemcpyDeviceToHost, c->stream));
   SC_TRY(c, cudaMemsetAsync(c->dstats, 0, sizeof(DevStats), c->stream));
+  SC_TRY(c, cudaMemsetAsync(accGauss(c), 0, 16, c->stream));
   SC_TRY(c, cudaStreamSynchronize(c->stream));
+  memcpy(&c->gauss_res, &g[0], 8);
+  memcpy(&c->rho_max, &g[1], 8);
   memset(stats, 0, sizeof(*stats));
   for (int k = 0; k < 8; ++k) stats->k_hist[k] = (int64_t)h.k_hist[k];
   stats->substeps = (int64_t)h.substeps;

@@ -586,11 +586,29 @@ __global__ void __launch_bounds__(kThreads, PIC_BINNED_MIN_BLOCKS) push_binned_k
     }
   };
 
+  // Work items: a warp's first item is its warp-major index (no atomic: the
+  // heavy items, first in the order, spread over the SMs); later ones come
+  // from the cursor, offset by the number of warps.  In the stream the next
+  // claim is issued one item ahead (lane 0 holds it), so the atomic's round
+  // trip overlaps the current item's work instead of stalling the warp.
+  const int64_t n_warps = (int64_t)gridDim.x * kWarps;
+  bool first_claim = true;
   auto claim = [&]() -> int64_t {
-    if (lane == 0) s_task[warp] = atomicAdd(a.cursor, 1);
-    __syncwarp();
-    const int64_t t = s_task[warp];
-    __syncwarp();
+    if (first_claim) {
+      first_claim = false;
+      return (int64_t)warp * gridDim.x + blockIdx.x;
+    }
+    int v = 0;
+    if (lane == 0) v = atomicAdd(a.cursor, 1);
+    return n_warps + __shfl_sync(0xffffffffu, v, 0);
+  };
+  int ahead = 0;  // lane 0: the claim issued one item ahead
+  auto claim_ahead = [&]() {
+    if (lane == 0) ahead = atomicAdd(a.cursor, 1);
+  };
+  auto take_ahead = [&]() -> int64_t {
+    const int64_t t = n_warps + __shfl_sync(0xffffffffu, ahead, 0);
+    claim_ahead();
     return t;
   };
 
@@ -639,10 +657,11 @@ __global__ void __launch_bounds__(kThreads, PIC_BINNED_MIN_BLOCKS) push_binned_k
     int64_t gen_next = (t - n_pred_end) * kTilesPerItem;
     int64_t gen_end = gen_next + kTilesPerItem < n_tiles ? gen_next + kTilesPerItem : n_tiles;
     bool gen_done = false;
+    claim_ahead();
     auto gen = [&]() -> int64_t {  // next tile of this warp, -1 when the stream is exhausted
       if (gen_done) return -1;
       if (gen_next >= gen_end) {
-        const int64_t it = claim();
+        const int64_t it = take_ahead();
         if (it >= n_items) {
           gen_done = true;
           return -1;
@@ -706,6 +725,9 @@ __global__ void __launch_bounds__(kThreads, PIC_BINNED_MIN_BLOCKS) push_binned_k
     }
   }
 
+  // the claim issued ahead must have been performed before the block reports
+  // done (the last block resets the cursor): consuming its value waits for it
+  if (lane == 0) s_task[warp] = ahead;
   // push what is left in the stashes
   drain(true);
   flush_counters(tc, sh, a.stats);
