@@ -641,6 +641,15 @@ def run_learned(args, make, start, Wu, K, last, n_e, ws, stream):
     pred0 = torch.empty(n_e, dtype=torch.uint8, device="cuda")
     native.predict(integ, net, start + Wu - 1, pred0)
     pred_hist = torch.bincount(pred0.long(), minlength=8).tolist()
+    # the prediction pass alone (features + network on the tensor cores), 5 times
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(5):
+        native.predict(integ, net, start + Wu - 1, pred0)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    predict_ms = p0.elapsed_time(p1) / 5
     del pred0
     torch.cuda.synchronize()
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
@@ -652,6 +661,9 @@ def run_learned(args, make, start, Wu, K, last, n_e, ws, stream):
              "kern_ms": kern_ms, "clocks": clk,
              "predict_every": args.predict_every, "gpu_launches": launches,
              "predicted_k_hist_first_step": pred_hist,
+             "predict_ms": predict_ms,
+             "predict_note": "pic_predict of every electron (features + MLP on tcgen05, TMEM "
+                             "accumulators), CUDA events, mean of 5",
              "training": {"pairs": int(len(Y)), "held_out_accuracy": acc,
                           "same_k_as_last_step_accuracy": acc_prev,
                           "k_ge_3_recall": heavy_recall, "k_ge_3_false_alarm_rate": false_alarm,

@@ -94,8 +94,14 @@ typedef struct {
                            stream and then catches up (the same bits either
                            way; a call finishes every particle).  0: 256;
                            < 0: no limit                                      */
-  int32_t reserved[2];
+  int32_t diagnostics; /* PIC_FP64 form: PIC_DIAG_WORK accumulates, per particle,
+                          the work of the electric field over every Boris push
+                          (App. B; read with pic_work_read); 0: none          */
+  int32_t reserved;
 } pic_params;
+
+/* pic_params.diagnostics */
+#define PIC_DIAG_WORK 1
 
 typedef struct {
   int64_t k_hist[8];      /* macro steps taken with each k                       */
@@ -153,6 +159,16 @@ int pic_fields_upload(pic_ctx* ctx, int64_t level, int64_t i0, const double* Ey,
  * nothing synchronizes and the counters keep accumulating (pic_stats_read).
  * Errors: PIC_EINVAL, PIC_ECUDA, PIC_ERANGE, PIC_EKMAX, PIC_ETIMEOUT. */
 int pic_push_step(pic_ctx* ctx, int64_t n, int64_t n_steps, pic_step_stats* stats);
+
+/* Energy-balance diagnostic (App. B, Eqs. EQ_35A, eq:ke_nosub,
+ * eq:work_nosub), FP64 form with diagnostics = PIC_DIAG_WORK: the work the
+ * electric field has done on each of the first n particles since
+ * pic_particles_write (which zeroes it), summed over every Boris push as
+ * (q hp / 2) E' . (v_before + v_after), with hp the push's momentum step
+ * (the transitional (h_old + h)/2 or h), E' its field and v = p/gamma before
+ * and after it; compare with the kinetic energy gamma - 1.  work: n FP64 in
+ * `where` memory.  Errors: PIC_EINVAL (not enabled), PIC_ECUDA. */
+int pic_work_read(pic_ctx* ctx, double* work, int64_t n, int32_t where);
 
 /* Read (and optionally reset) the accumulated counters.  Synchronizes. */
 int pic_stats_read(pic_ctx* ctx, pic_step_stats* stats, int32_t reset);

@@ -71,7 +71,7 @@ def lib():
         _lib.orc_boris.argtypes = [p, d, d, d, d]
         _lib.orc_boris.restype = None
         _lib.orc_push_step.argtypes = [ctypes.POINTER(OrcParams), i64, p, p, p, p, p,
-                                       p, p, p, p, i64, ctypes.POINTER(OrcStats)]
+                                       p, p, p, p, i64, ctypes.POINTER(OrcStats), p]
         _lib.orc_push_step.restype = i64
     return _lib
 
@@ -130,7 +130,7 @@ class Particles:
 
 
 def push_step(prm: Params, parts: Particles, E_lv: np.ndarray, E_i0, B_lv: np.ndarray, B_i0,
-              stats: OrcStats | None = None) -> OrcStats:
+              stats: OrcStats | None = None, work: np.ndarray | None = None) -> OrcStats:
     """One macro step of Algorithm 1 over all particles.
 
     E_lv, B_lv: (p+1, W) float64, ascending time (E levels n-p..n, B levels
@@ -146,9 +146,11 @@ def push_step(prm: Params, parts: Particles, E_lv: np.ndarray, E_i0, B_lv: np.nd
     assert e0.shape == (p + 1,) and b0.shape == (p + 1,)
     st = stats if stats is not None else OrcStats()
     c = prm.c()
+    if work is not None:
+        assert work.dtype == np.float64 and work.flags["C_CONTIGUOUS"] and work.shape == (parts.n,)
     lib().orc_push_step(ctypes.byref(c), parts.n, _ptr(parts.x), _ptr(parts.px), _ptr(parts.py),
                         _ptr(parts.pz), _ptr(parts.status), _ptr(E_lv), _ptr(e0), _ptr(B_lv),
-                        _ptr(b0), W, ctypes.byref(st))
+                        _ptr(b0), W, ctypes.byref(st), None if work is None else _ptr(work))
     return st
 
 
@@ -157,7 +159,7 @@ def _bind_run():
     if not hasattr(L, "_run_bound"):
         d, i64, p = ctypes.c_double, ctypes.c_int64, ctypes.c_void_p
         L.orc_run.argtypes = [ctypes.POINTER(OrcParams), i64, i64, p, p, p, p, p, p, p, p, p, i64,
-                              p, p, ctypes.POINTER(OrcStats)]
+                              p, p, ctypes.POINTER(OrcStats), p]
         L.orc_run.restype = i64
         L._run_bound = True
     return L
@@ -165,7 +167,7 @@ def _bind_run():
 
 def run(prm: Params, parts: Particles, E_all: np.ndarray, E_i0_all, B_all: np.ndarray, B_i0_all,
         stats: OrcStats | None = None, r_ref: np.ndarray | None = None,
-        r_dev: np.ndarray | None = None) -> OrcStats:
+        r_dev: np.ndarray | None = None, work: np.ndarray | None = None) -> OrcStats:
     """len(E_all) - p consecutive macro steps; row r of E_all/B_all is level n0 - p + r.
 
     r_ref/r_dev: optional per-particle dephasing reference and running max of
@@ -184,7 +186,10 @@ def run(prm: Params, parts: Particles, E_all: np.ndarray, E_i0_all, B_all: np.nd
     c = prm.c()
     rr = None if r_ref is None else _ptr(r_ref)
     rd = None if r_dev is None else _ptr(r_dev)
+    if work is not None:
+        assert work.dtype == np.float64 and work.flags["C_CONTIGUOUS"] and work.shape == (parts.n,)
     _bind_run().orc_run(ctypes.byref(c), n_steps, parts.n, _ptr(parts.x), _ptr(parts.px),
                         _ptr(parts.py), _ptr(parts.pz), _ptr(parts.status), _ptr(E_all), _ptr(e0),
-                        _ptr(B_all), _ptr(b0), W, rr, rd, ctypes.byref(st))
+                        _ptr(B_all), _ptr(b0), W, rr, rd, ctypes.byref(st),
+                        None if work is None else _ptr(work))
     return st

@@ -137,13 +137,17 @@ static int orc_in_window(double s, const int64_t* i0, int64_t W, int32_t p) {
  * temporal interpolation of Sec. VI.
  *   E_lv: (p+1) x W, E levels n-p .. n (ascending), origins E_i0[p+1]
  *   B_lv: (p+1) x W, B levels n+1/2-p .. n+1/2,       origins B_i0[p+1]
+ *   work: NULL, or per particle the work of the electric field accumulated
+ *         over every Boris push (App. B, Eq. eq:work_nosub, taken per sub-step):
+ *         w = (q hp / 2) E' . (v_before + v_after), v = p / gamma of the
+ *         momentum before and after the push, hp its step.
  * Returns the number of particles that left the window during this step.
  */
 int64_t orc_push_step(const orc_params* prm, int64_t n,
                       double* x, double* px, double* py, double* pz, uint8_t* status,
                       const double* E_lv, const int64_t* E_i0,
                       const double* B_lv, const int64_t* B_i0, int64_t W,
-                      orc_stats* st) {
+                      orc_stats* st, double* work) {
   const int32_t p = prm->order;
   const double dt = prm->dt;
   const double inv_dx = 1.0 / prm->dx;
@@ -194,8 +198,14 @@ int64_t orc_push_step(const orc_params* prm, int64_t n,
       orc_gather(E_lv, E_i0, W, p, wE, s, &ey);
       orc_gather(B_lv, B_i0, W, p, wB, sb, &bz);
       double hp = (j == 1) ? 0.5 * (h_old + h) : h;
+      double vy_before = 0.0;
+      if (work) {
+        double gb = sqrt(1.0 + (pv[0] * pv[0] + pv[1] * pv[1] + pv[2] * pv[2]));
+        vy_before = pv[1] / gb;
+      }
       orc_boris(pv, ey, bz, hp, prm->qm);
       double g = sqrt(1.0 + (pv[0] * pv[0] + pv[1] * pv[1] + pv[2] * pv[2]));
+      if (work) work[i] = work[i] + ((prm->qm * hp) * 0.5) * (ey * (vy_before + pv[1] / g));
       xi = xi + h * (pv[0] / g);                     /* Eqs. eq:gamma - eq:x */
     }
     x[i] = xi; px[i] = pv[0]; py[i] = pv[1]; pz[i] = pv[2];
@@ -212,17 +222,18 @@ int64_t orc_push_step(const orc_params* prm, int64_t n,
  * dephasing diagnostic of Eq. R error (Sec. IV) is accumulated per particle:
  * r_dev[i] = max over steps of |(gamma - p_x) - r_ref[i]| evaluated on the
  * momentum after each macro step (r_ref = 1 for an electron starting at rest;
- * for another start, gamma_0 - p_x0, App. A).  r_ref / r_dev may be NULL.
+ * for another start, gamma_0 - p_x0, App. A).  r_ref / r_dev may be NULL;
+ * work as for orc_push_step.
  */
 int64_t orc_run(const orc_params* prm, int64_t n_steps, int64_t n,
                 double* x, double* px, double* py, double* pz, uint8_t* status,
                 const double* E_all, const int64_t* E_i0_all,
                 const double* B_all, const int64_t* B_i0_all, int64_t W,
-                const double* r_ref, double* r_dev, orc_stats* st) {
+                const double* r_ref, double* r_dev, orc_stats* st, double* work) {
   int64_t lost = 0;
   for (int64_t s = 0; s < n_steps; ++s) {
     lost += orc_push_step(prm, n, x, px, py, pz, status, E_all + s * W, E_i0_all + s,
-                          B_all + s * W, B_i0_all + s, W, st);
+                          B_all + s * W, B_i0_all + s, W, st, work);
     if (r_ref && r_dev) {
       for (int64_t i = 0; i < n; ++i) {
         double g = sqrt(1.0 + (px[i] * px[i] + py[i] * py[i] + pz[i] * pz[i]));

@@ -11,13 +11,15 @@ Metrics (per electron, then over the ensemble), against an FP64 reference:
   displacement: max |x - x_ref| / max(|x_ref - x0|, 1)
 
 Unresolved fronts.  Where the wave is switched on with a jump no grid
-resolves, the FP64 method itself is hypersensitive: an initial state perturbed
-by a few FP32 units in the last place already moves a fraction of the electrons
-past dp = 1e-4.  There the mixed form is held to a backward-error bound: its
-error (against the FP64 form started from the same, FP32-rounded, state) may be
-no worse than the FP64 form's own response to a perturbation of the initial
-state by `ulps` FP32 units in the last place (positions by ulps * 2^-24 cells,
-momenta by a factor 1 + ulps * 2^-24, signs from a fixed seed).
+resolves, the FP64 method itself is hypersensitive: inputs perturbed by a few
+FP32 units in the last place already move a fraction of the electrons past
+dp = 1e-4.  There the mixed form is held to a backward-error bound: its error
+(against the FP64 form started from the same, FP32-rounded, state) may be no
+worse than the FP64 form's own response to a perturbation of its inputs by
+`ulps` FP32 units in the last place: every field level value by a factor
+1 + ulps * 2^-24 (the mixed form stores the fields in FP32), positions by
+ulps * 2^-24 cells and momenta by a factor 1 + ulps * 2^-24 (signs from fixed
+seeds).
 """
 from __future__ import annotations
 
@@ -55,6 +57,17 @@ def perturbed(init, dx, ulps, seed=11):
         else:
             out.append(a * (1 + s * (ulps * U32)))
     return out
+
+
+def perturbed_levels(L, ulps, seed):
+    """Field levels (rows of an array or tensor) with every value moved by a
+    factor 1 +- ulps 2^-24, on the device."""
+    import torch
+    t = torch.as_tensor(L, device="cuda", dtype=torch.float64)
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    s = (torch.randint(0, 2, tuple(t.shape), generator=g, dtype=torch.int8) * 2 - 1).to(
+        device=t.device, dtype=t.dtype)
+    return t * (1 + s * (ulps * U32))
 
 
 def run_form(native, wl, precision, schedule, init, steps, E, B, i0, ring, stream, heavy_budget=0):
@@ -116,8 +129,11 @@ def front_accuracy(native, wl, init, steps, E, B, i0, ring, stream, schedule,
             "what": "FP64 run from the FP32-rounded initial state vs FP64 run",
             **compare(ref_r, ref, init[0], wl.a0)}
         for u in ulps:
+            Eu = perturbed_levels(E, u, seed=101)
+            Bu = perturbed_levels(B, u, seed=202)
             ref_u = run_form(native, wl, native.PIC_FP64, native.PIC_SCHED_PLAIN,
-                             perturbed(init, wl.dx, u), steps, E, B, i0, ring, stream)
+                             perturbed(init, wl.dx, u), steps, Eu, Bu, i0, ring, stream)
+            del Eu, Bu
             res[f"fp64_perturbed_{u}ulp"] = compare(ref_u, ref, init[0], wl.a0)
     return res
 
@@ -130,8 +146,8 @@ BACKWARD_ULPS = 4
 def backward_error_ok(res, ulps=BACKWARD_ULPS):
     """The unresolved-front criterion on a front_accuracy(unresolved=True)
     result: the mixed form, against the FP64 form from the same rounded start,
-    puts no more electrons past dp = 1e-4 than the FP64 form perturbed by `ulps`
-    FP32 ulps does (with a Poisson allowance of 3 sigma + 3 electrons for small
+    puts no more electrons past dp = 1e-4 than the FP64 form with its inputs
+    (fields and start) perturbed by `ulps` FP32 ulps does (with a Poisson allowance of 3 sigma + 3 electrons for small
     ensembles), its 99.9th percentile of dp is no larger when the ensemble has
     at least 10^5 electrons, and the energy gains agree to 0.1 %.
     Returns (ok, reason)."""

@@ -29,6 +29,7 @@ SOURCES = {
     "batch_api.cu": [],
     "mlp_bf16.cu": [],
     "mlp_api.cu": [],
+    "mlp_tc.cu": [],
     "pic_sc1d.cu": ["-fmad=false"],
 }
 

@@ -9,12 +9,14 @@
 // z = h2 W3^T + b3; W_l is (out, in).  phi = (asinh|E|, asinh|B|, asinh p_x,
 // asinh p_y, asinh p_z, log gamma).
 //
-// Tensor cores: mma.sync m16n8k16 (BF16 in, FP32 accumulate), 16 particles per
-// warp tile.  A layer's accumulator fragments are, after bias and ReLU, exactly
-// the next layer's A fragments, so hidden activations never leave registers in
-// the forward pass.  Backward: dz on the CUDA cores, dh2 = dz W3 and
-// dh1 = da2 W2 on the tensor cores, weight gradients (batch reductions) from
-// BF16-rounded operands with FP32 accumulation in shared memory.
+// Training (this file): warp-level mma.sync m16n8k16 (BF16 in, FP32
+// accumulate), 16 samples per warp tile.  A layer's accumulator fragments are,
+// after bias and ReLU, exactly the next layer's A fragments, so hidden
+// activations never leave registers in the forward pass.  Backward: dz on the
+// CUDA cores, dh2 = dz W3 and dh1 = da2 W2 on the tensor cores, weight
+// gradients (batch reductions) from BF16-rounded operands with FP32
+// accumulation in shared memory.  Inference (mlp_tc.cu) runs on tcgen05 with
+// TMEM accumulators.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -156,181 +158,7 @@ __device__ __forceinline__ void phi_fragment(const float* phi, int64_t n, int64_
   a1[3] = 0u;
 }
 
-// Argmax over the 8 logits of rows g and g+8 (ties: lowest class).
-__device__ __forceinline__ void argmax_rows(const float (&z)[4], int& c0, int& c1) {
-  const int t = threadIdx.x & 3;
-  float v0 = z[0], v1 = z[2];
-  int i0 = 2 * t, i1 = 2 * t;
-  if (z[1] > v0) { v0 = z[1]; i0 = 2 * t + 1; }
-  if (z[3] > v1) { v1 = z[3]; i1 = 2 * t + 1; }
-#pragma unroll
-  for (int o = 1; o <= 2; o <<= 1) {
-    const float w0 = __shfl_xor_sync(0xffffffffu, v0, o);
-    const int j0 = __shfl_xor_sync(0xffffffffu, i0, o);
-    const float w1 = __shfl_xor_sync(0xffffffffu, v1, o);
-    const int j1 = __shfl_xor_sync(0xffffffffu, i1, o);
-    if (w0 > v0 || (w0 == v0 && j0 < i0)) { v0 = w0; i0 = j0; }
-    if (w1 > v1 || (w1 == v1 && j1 < i1)) { v1 = w1; i1 = j1; }
-  }
-  c0 = i0;
-  c1 = i1;
-}
-
 }  // namespace
-
-// ---------------------------------------------------------------- inference
-
-__global__ void __launch_bounds__(128) mlp_infer_kernel(const float* P, const float* phi, int64_t n,
-                                                        uint8_t* pred) {
-  __shared__ SmemW s;
-  load_weights(s, P);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t tile = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-       tile * 16 < n; tile += warps) {
-    const int64_t base = tile * 16;
-    uint32_t a1[4];
-    phi_fragment(phi, n, base, a1);
-    Fwd f;
-    forward_tile(s, a1, f);
-    int c0, c1;
-    argmax_rows(f.z, c0, c1);
-    if (t == 0) {
-      if (base + g < n) pred[base + g] = (uint8_t)c0;
-      if (base + g + 8 < n) pred[base + g + 8] = (uint8_t)c1;
-    }
-  }
-}
-
-// ---------------------------------------------------------------- fused features + inference
-
-namespace {
-
-// Inference-only forward of two 16-row tiles that share every weight fragment
-// load; the same MMA sequence per tile as forward_tile, so the same logits.
-__device__ __forceinline__ void infer_tiles2(const SmemW& s, const uint32_t (&x0)[4],
-                                             const uint32_t (&x1)[4], float (&z0)[4],
-                                             float (&z1)[4]) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  uint32_t h0[4][4], h1[4][4];
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    const float bl = s.b1[8 * nt + 2 * t], bh = s.b1[8 * nt + 2 * t + 1];
-    float c0[4] = {bl, bh, bl, bh}, c1[4] = {bl, bh, bl, bh};
-    const __nv_bfloat16* w = s.W1p + (8 * nt + g) * kS1;
-    const uint32_t b0 = ld32(w + 2 * t), b1 = ld32(w + 2 * t + 8);
-    mma16816(c0, x0, b0, b1);
-    mma16816(c1, x1, b0, b1);
-    const int kc = nt >> 1, hi = (nt & 1) * 2;
-    h0[kc][hi] = pack2(fmaxf(c0[0], 0.f), fmaxf(c0[1], 0.f));
-    h0[kc][hi + 1] = pack2(fmaxf(c0[2], 0.f), fmaxf(c0[3], 0.f));
-    h1[kc][hi] = pack2(fmaxf(c1[0], 0.f), fmaxf(c1[1], 0.f));
-    h1[kc][hi + 1] = pack2(fmaxf(c1[2], 0.f), fmaxf(c1[3], 0.f));
-  }
-  uint32_t q0[4][4], q1[4][4];
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    const float bl = s.b2[8 * nt + 2 * t], bh = s.b2[8 * nt + 2 * t + 1];
-    float c0[4] = {bl, bh, bl, bh}, c1[4] = {bl, bh, bl, bh};
-    const __nv_bfloat16* w = s.W2 + (8 * nt + g) * kS2;
-#pragma unroll
-    for (int kc = 0; kc < 4; ++kc) {
-      const uint32_t b0 = ld32(w + 16 * kc + 2 * t), b1 = ld32(w + 16 * kc + 2 * t + 8);
-      mma16816(c0, h0[kc], b0, b1);
-      mma16816(c1, h1[kc], b0, b1);
-    }
-    const int kc = nt >> 1, hi = (nt & 1) * 2;
-    q0[kc][hi] = pack2(fmaxf(c0[0], 0.f), fmaxf(c0[1], 0.f));
-    q0[kc][hi + 1] = pack2(fmaxf(c0[2], 0.f), fmaxf(c0[3], 0.f));
-    q1[kc][hi] = pack2(fmaxf(c1[0], 0.f), fmaxf(c1[1], 0.f));
-    q1[kc][hi + 1] = pack2(fmaxf(c1[2], 0.f), fmaxf(c1[3], 0.f));
-  }
-  const float bl = s.b3[2 * t], bh = s.b3[2 * t + 1];
-  z0[0] = bl; z0[1] = bh; z0[2] = bl; z0[3] = bh;
-  z1[0] = bl; z1[1] = bh; z1[2] = bl; z1[3] = bh;
-  const __nv_bfloat16* w = s.W3 + g * kS2;
-#pragma unroll
-  for (int kc = 0; kc < 4; ++kc) {
-    const uint32_t b0 = ld32(w + 16 * kc + 2 * t), b1 = ld32(w + 16 * kc + 2 * t + 8);
-    mma16816(z0, q0[kc], b0, b1);
-    mma16816(z1, q1[kc], b0, b1);
-  }
-}
-
-}  // namespace
-
-// Features and prediction in one pass: each warp takes 32 particles (one per
-// lane), forms their features in registers (particle_features, the same code
-// as the features kernel), passes them through a per-warp shared-memory tile
-// into the layer-1 fragments of two 16-row tiles and writes the argmax class.
-// The same predictions as the features kernel followed by mlp_infer_kernel,
-// without the 24 bytes per particle of features going through HBM.
-template <int P>
-// Four resident blocks per SM (at most 128 registers a thread): measured
-// faster than the register-unbounded build at three.
-#ifndef PIC_PREDICT_MIN_BLOCKS
-#define PIC_PREDICT_MIN_BLOCKS 4
-#endif
-__global__ void __launch_bounds__(128, PIC_PREDICT_MIN_BLOCKS) predict_kernel(PushArgsMixed a, const float* Pm,
-                                                      uint8_t* pred) {
-  __shared__ SmemW s;
-  __shared__ float ft[4][32][8];
-  load_weights(s, Pm);
-  __syncthreads();
-  StepFields<P, true> F;
-  load_fields<P, true>(F, a, false);
-  float w[2 * (P + 1)];
-  lagrange_f32<P>(1.5f, w);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-  float(&T)[32][8] = ft[warp];
-  T[lane][6] = 0.f;
-  T[lane][7] = 0.f;
-  const int64_t stride = (int64_t)gridDim.x * (blockDim.x >> 5) * 32;
-  for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * 32; base < a.n;
-       base += stride) {
-    float f[6];
-    particle_features<P>(a, F, w, base + lane, f);
-#pragma unroll
-    for (int q = 0; q < 6; ++q) T[lane][q] = f[q];
-    __syncwarp();
-    uint32_t x0[4], x1[4];
-    x0[0] = pack2(T[g][2 * t], T[g][2 * t + 1]);
-    x0[1] = pack2(T[g + 8][2 * t], T[g + 8][2 * t + 1]);
-    x1[0] = pack2(T[g + 16][2 * t], T[g + 16][2 * t + 1]);
-    x1[1] = pack2(T[g + 24][2 * t], T[g + 24][2 * t + 1]);
-    x0[2] = x0[3] = x1[2] = x1[3] = 0u;
-    __syncwarp();
-    float z0[4], z1[4];
-    infer_tiles2(s, x0, x1, z0, z1);
-    int c0, c1, c2, c3;
-    argmax_rows(z0, c0, c1);
-    argmax_rows(z1, c2, c3);
-    if (t == 0) {
-      if (base + g < a.n) pred[base + g] = (uint8_t)c0;
-      if (base + g + 8 < a.n) pred[base + g + 8] = (uint8_t)c1;
-      if (base + g + 16 < a.n) pred[base + g + 16] = (uint8_t)c2;
-      if (base + g + 24 < a.n) pred[base + g + 24] = (uint8_t)c3;
-    }
-  }
-}
-
-cudaError_t launch_predict_fused(const PushArgsMixed& a, int order, const float* P, uint8_t* pred,
-                                 int sm_count, cudaStream_t st) {
-  if (a.n <= 0) return cudaSuccess;
-  const int64_t want = (a.n + 127) / 128;
-  const int64_t cap = (int64_t)(sm_count > 0 ? sm_count : 152) * 8;
-  const int blocks = (int)(want < cap ? want : cap);
-  switch (order) {
-    case 1: predict_kernel<1><<<blocks, 128, 0, st>>>(a, P, pred); break;
-    case 2: predict_kernel<2><<<blocks, 128, 0, st>>>(a, P, pred); break;
-    case 3: predict_kernel<3><<<blocks, 128, 0, st>>>(a, P, pred); break;
-    case 4: predict_kernel<4><<<blocks, 128, 0, st>>>(a, P, pred); break;
-    case 5: predict_kernel<5><<<blocks, 128, 0, st>>>(a, P, pred); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
-}
 
 // ---------------------------------------------------------------- training (gradients)
 
@@ -523,17 +351,6 @@ int mlp_param_count() { return kNParams; }
 size_t mlp_grad_smem(int warps) {
   return ((sizeof(SmemW) + 15) & ~(size_t)15) + (size_t)warps * sizeof(WarpStage) +
          (size_t)kNParams * sizeof(float);
-}
-
-cudaError_t launch_mlp_infer(const float* P, const float* phi, int64_t n, uint8_t* pred,
-                             int sm_count, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  const int64_t tiles = (n + 15) / 16;
-  int64_t blocks = (tiles + 3) / 4;
-  const int64_t cap = (int64_t)(sm_count > 0 ? sm_count : 152) * 8;
-  if (blocks > cap) blocks = cap;
-  mlp_infer_kernel<<<(int)blocks, 128, 0, s>>>(P, phi, n, pred);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_mlp_grad(const float* P, const float* phi, const uint8_t* label, int64_t n,

@@ -1,0 +1,373 @@
+// Inference of the sub-cycle-count predictor on the 5th-generation tensor
+// cores: tcgen05.mma with operands in shared memory and FP32 accumulators in
+// tensor memory (TMEM).  Not part of the paper: the network only predicts the
+// exponent k the criterion of Sec. IV will pick next, for binning; the
+// criterion still decides every sub-step.
+//
+// Per CTA (128 threads, one warpgroup) and tile of 128 particles:
+//   features: each thread forms one particle's phi (6 values, BF16, zero-
+//     padded to K = 16) and stores it as row r of A1 [128 x 16];
+//   layer 1: one tcgen05.mma M=128 N=64 K=16, A1 x W1^T -> D1 (TMEM cols 0..63);
+//   epilogue 1: each warp reads its 32 TMEM lanes (rows) with tcgen05.ld, adds
+//     b1, applies ReLU, rounds to BF16 and writes A2 [128 x 64];
+//   layer 2: four MMAs (K = 16 each) A2 x W2^T -> D2 (cols 64..127);
+//   epilogue 2: b2, ReLU, BF16 -> A2 again (layer 2 has read it);
+//   layer 3: four MMAs A2 x W3^T (N = 16, rows 8..15 of W3 zero) -> D3 (cols 0..15);
+//   epilogue 3: b3, argmax over the 8 classes (ties: the smaller k).
+// One thread issues the MMAs and commits them to an mbarrier that every
+// thread waits on (a bounded wait: on a give-up the CTA records it, marks its
+// remaining predictions 0xFF, an invalid class, frees its TMEM and returns).
+//
+// Shared-memory operands use the no-swizzle K-major layout of 8 x 16-byte
+// core matrices: element (r, k) of an R x K tile sits at
+// (r / 8) * (K / 8) * 128 + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2 bytes;
+// the descriptors give the step between core matrices along K (128 B) and
+// along R ((K / 8) * 128 B).
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "pic_internal.h"
+#include "push_device.cuh"
+
+namespace pic {
+namespace {
+
+constexpr int kTcRows = 128;  // particles per tile (MMA M)
+constexpr int kTcH = 64, kTcIn = 6, kTcOut = 8;
+constexpr uint32_t kTmemCols = 128;
+
+struct TcSmem {
+  __align__(1024) unsigned char W1[kTcH * 16 * 2];    // [64 x 16]
+  __align__(1024) unsigned char W2[kTcH * kTcH * 2];  // [64 x 64]
+  __align__(1024) unsigned char W3[16 * kTcH * 2];    // [16 x 64], rows 8..15 zero
+  __align__(1024) unsigned char A1[kTcRows * 16 * 2];     // [128 x 16]
+  __align__(1024) unsigned char A2[kTcRows * kTcH * 2];   // [128 x 64]
+  float b1[kTcH], b2[kTcH], b3[kTcOut];
+  __align__(8) uint64_t bar;
+  uint32_t tmem;
+  int failed;
+};
+// Reserved per CTA so that at most four CTAs share an SM: four 128-column
+// TMEM allocations fill its 512 columns, so an allocation never waits.
+constexpr size_t kTcSmemBytes = 48 * 1024;
+static_assert(sizeof(TcSmem) + 1024 <= kTcSmemBytes, "tile buffers fit the reservation");
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t cm_off(int r, int k, int K) {
+  return (uint32_t)(r >> 3) * (uint32_t)(K / 8) * 128u + (uint32_t)(k >> 3) * 128u +
+         (uint32_t)(r & 7) * 16u + (uint32_t)(k & 7) * 2u;
+}
+
+// Shared-memory matrix descriptor (no swizzle): start address, the byte step
+// between core matrices along K (leading) and along the rows (stride), and the
+// descriptor version of this architecture.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t k_step, uint32_t r_step) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((k_step >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((r_step >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N and M.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         int accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Bounded wait for phase `parity` of the barrier: false = gave up.
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 22); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(saddr(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// 16 consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ uint32_t bf2(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// Packed FP32 master parameters (W1[64][6] b1[64] W2[64][64] b2[64] W3[8][64]
+// b3[8]) to BF16 operand tiles and FP32 biases.
+__device__ void tc_load_weights(TcSmem& s, const float* P) {
+  const float* W1 = P;
+  const float* b1 = W1 + kTcH * kTcIn;
+  const float* W2 = b1 + kTcH;
+  const float* b2 = W2 + kTcH * kTcH;
+  const float* W3 = b2 + kTcH;
+  const float* b3 = W3 + kTcOut * kTcH;
+  for (int e = threadIdx.x; e < kTcH * 16; e += blockDim.x) {
+    const int o = e / 16, i = e % 16;
+    *reinterpret_cast<__nv_bfloat16*>(s.W1 + cm_off(o, i, 16)) =
+        __float2bfloat16_rn(i < kTcIn ? W1[o * kTcIn + i] : 0.0f);
+  }
+  for (int e = threadIdx.x; e < kTcH * kTcH; e += blockDim.x) {
+    const int o = e / kTcH, i = e % kTcH;
+    *reinterpret_cast<__nv_bfloat16*>(s.W2 + cm_off(o, i, kTcH)) = __float2bfloat16_rn(W2[e]);
+  }
+  for (int e = threadIdx.x; e < 16 * kTcH; e += blockDim.x) {
+    const int o = e / kTcH, i = e % kTcH;
+    *reinterpret_cast<__nv_bfloat16*>(s.W3 + cm_off(o, i, kTcH)) =
+        __float2bfloat16_rn(o < kTcOut ? W3[o * kTcH + i] : 0.0f);
+  }
+  for (int e = threadIdx.x; e < kTcH; e += blockDim.x) {
+    s.b1[e] = b1[e];
+    s.b2[e] = b2[e];
+  }
+  if (threadIdx.x < kTcOut) s.b3[threadIdx.x] = b3[threadIdx.x];
+}
+
+// Row r of A1 from this thread's features (BF16, columns 6..15 zero).
+__device__ __forceinline__ void put_features(TcSmem& s, int r, const float (&f)[6]) {
+  uint4 lo, hi;
+  lo.x = bf2(f[0], f[1]);
+  lo.y = bf2(f[2], f[3]);
+  lo.z = bf2(f[4], f[5]);
+  lo.w = 0u;
+  hi = make_uint4(0u, 0u, 0u, 0u);
+  *reinterpret_cast<uint4*>(s.A1 + cm_off(r, 0, 16)) = lo;
+  *reinterpret_cast<uint4*>(s.A1 + cm_off(r, 8, 16)) = hi;
+}
+
+// Hidden layer epilogue: accumulator columns [c0, c0 + 64) of row r, plus
+// bias, ReLU, BF16, into row r of A2.
+__device__ __forceinline__ void hidden_epilogue(TcSmem& s, uint32_t lane_addr, int c0,
+                                                const float* bias, int r) {
+#pragma unroll
+  for (int blk = 0; blk < 4; ++blk) {
+    float v[16];
+    tmem_ld16(lane_addr + (uint32_t)(c0 + 16 * blk), v);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = fmaxf(v[q] + bias[16 * blk + q], 0.f);
+    uint4 w0 = make_uint4(bf2(v[0], v[1]), bf2(v[2], v[3]), bf2(v[4], v[5]), bf2(v[6], v[7]));
+    uint4 w1 = make_uint4(bf2(v[8], v[9]), bf2(v[10], v[11]), bf2(v[12], v[13]), bf2(v[14], v[15]));
+    *reinterpret_cast<uint4*>(s.A2 + cm_off(r, 16 * blk, kTcH)) = w0;
+    *reinterpret_cast<uint4*>(s.A2 + cm_off(r, 16 * blk + 8, kTcH)) = w1;
+  }
+}
+
+// The network on the tile whose row r (this thread) carries features f;
+// returns the class (argmax, ties to the smaller k) or 0xFF after a give-up.
+// Collective over the CTA.  `ph` is the mbarrier phase, advanced per commit.
+__device__ __forceinline__ int tc_tile(TcSmem& s, const float (&f)[6], uint32_t& ph) {
+  const int r = threadIdx.x;
+  const int warp = threadIdx.x >> 5;
+  put_features(s, r, f);
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t lane_addr = s.tmem + ((uint32_t)(32 * warp) << 16);
+  bool ok = !s.failed;
+  // layer 1
+  if (ok && threadIdx.x == 0) {
+    mma_bf16(s.tmem, sdesc(saddr(s.A1), 128, 256), sdesc(saddr(s.W1), 128, 256),
+             idesc_bf16(kTcRows, kTcH), 0);
+    mma_commit(&s.bar);
+  }
+  if (ok) { ok = bar_wait(&s.bar, ph); ph ^= 1u; }
+  fence_after();
+  if (ok) hidden_epilogue(s, lane_addr, 0, s.b1, r);
+  fence_async_smem();
+  fence_before();
+  if (!ok) s.failed = 1;
+  __syncthreads();
+  fence_after();
+  ok = !s.failed;
+  // layer 2
+  if (ok && threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      mma_bf16(s.tmem + kTcH, sdesc(saddr(s.A2) + 256u * k, 128, 1024),
+               sdesc(saddr(s.W2) + 256u * k, 128, 1024), idesc_bf16(kTcRows, kTcH), k > 0);
+    mma_commit(&s.bar);
+  }
+  if (ok) { ok = bar_wait(&s.bar, ph); ph ^= 1u; }
+  fence_after();
+  if (ok) hidden_epilogue(s, lane_addr, kTcH, s.b2, r);
+  fence_async_smem();
+  fence_before();
+  if (!ok) s.failed = 1;
+  __syncthreads();
+  fence_after();
+  ok = !s.failed;
+  // layer 3
+  if (ok && threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      mma_bf16(s.tmem, sdesc(saddr(s.A2) + 256u * k, 128, 1024),
+               sdesc(saddr(s.W3) + 256u * k, 128, 1024), idesc_bf16(kTcRows, 16), k > 0);
+    mma_commit(&s.bar);
+  }
+  if (ok) { ok = bar_wait(&s.bar, ph); ph ^= 1u; }
+  fence_after();
+  int cls = 0xFF;
+  if (ok) {
+    float z[16];
+    tmem_ld16(lane_addr, z);
+    float best = z[0] + s.b3[0];
+    cls = 0;
+#pragma unroll
+    for (int c = 1; c < kTcOut; ++c) {
+      const float v = z[c] + s.b3[c];
+      if (v > best) { best = v; cls = c; }
+    }
+  }
+  fence_before();
+  if (!ok) s.failed = 1;
+  __syncthreads();  // A1, A2 and the TMEM columns are reused by the next tile
+  fence_after();
+  return s.failed ? 0xFF : cls;
+}
+
+__device__ __forceinline__ void tc_begin(TcSmem& s, const float* P) {
+  tc_load_weights(s, P);
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&s.tmem)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&s.bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s.failed = 0;
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+}
+
+__device__ __forceinline__ void tc_end(TcSmem& s) {
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s.tmem), "r"(kTmemCols));
+}
+
+}  // namespace
+
+// pic_predict: features of every particle after step a's levels (theta = 3/2,
+// the same code as the features kernel) and the network's class, in one pass.
+template <int P>
+__global__ void __launch_bounds__(128) predict_tc_kernel(PushArgsMixed a, const float* Pm, uint8_t* pred) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  TcSmem& s = *reinterpret_cast<TcSmem*>(smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023));
+  tc_begin(s, Pm);
+  StepFields<P, true> F;
+  load_fields<P, true>(F, a, false);
+  float w[2 * (P + 1)];
+  lagrange_f32<P>(1.5f, w);
+  uint32_t ph = 0;
+  const int64_t n_tiles = (a.n + kTcRows - 1) / kTcRows;
+  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int64_t i = t * kTcRows + threadIdx.x;
+    float f[6];
+    particle_features<P>(a, F, w, i, f);
+    const int c = tc_tile(s, f, ph);
+    if (i < a.n) pred[i] = (uint8_t)c;
+    if (s.failed) break;
+  }
+  if (s.failed && threadIdx.x == 0 && a.stats) atomicExch(&a.stats->error, 2);
+  tc_end(s);
+}
+
+// pic_mlp_infer: the network's class of n feature rows phi[n][6].
+__global__ void __launch_bounds__(128) mlp_infer_tc_kernel(const float* Pm, const float* phi, int64_t n,
+                                                           uint8_t* pred) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  TcSmem& s = *reinterpret_cast<TcSmem*>(smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023));
+  tc_begin(s, Pm);
+  uint32_t ph = 0;
+  const int64_t n_tiles = (n + kTcRows - 1) / kTcRows;
+  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int64_t i = t * kTcRows + threadIdx.x;
+    float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (i < n) {
+#pragma unroll
+      for (int q = 0; q < 6; ++q) f[q] = phi[i * 6 + q];
+    }
+    const int c = tc_tile(s, f, ph);
+    if (i < n) pred[i] = (uint8_t)c;
+    if (s.failed) break;
+  }
+  tc_end(s);
+}
+
+static int tc_grid(int64_t n, int sm_count) {
+  const int64_t tiles = (n + kTcRows - 1) / kTcRows;
+  const int64_t cap = (int64_t)(sm_count > 0 ? sm_count : 152) * 4;
+  return (int)(tiles < cap ? tiles : cap);
+}
+
+template <class K>
+static cudaError_t tc_configure(K kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes);
+}
+
+cudaError_t launch_predict_fused(const PushArgsMixed& a, int order, const float* P, uint8_t* pred,
+                                 int sm_count, cudaStream_t st) {
+  if (a.n <= 0) return cudaSuccess;
+  const int blocks = tc_grid(a.n, sm_count);
+  cudaError_t e = cudaSuccess;
+  switch (order) {
+    case 1: e = tc_configure(predict_tc_kernel<1>); if (e == cudaSuccess) predict_tc_kernel<1><<<blocks, 128, kTcSmemBytes, st>>>(a, P, pred); break;
+    case 2: e = tc_configure(predict_tc_kernel<2>); if (e == cudaSuccess) predict_tc_kernel<2><<<blocks, 128, kTcSmemBytes, st>>>(a, P, pred); break;
+    case 3: e = tc_configure(predict_tc_kernel<3>); if (e == cudaSuccess) predict_tc_kernel<3><<<blocks, 128, kTcSmemBytes, st>>>(a, P, pred); break;
+    case 4: e = tc_configure(predict_tc_kernel<4>); if (e == cudaSuccess) predict_tc_kernel<4><<<blocks, 128, kTcSmemBytes, st>>>(a, P, pred); break;
+    case 5: e = tc_configure(predict_tc_kernel<5>); if (e == cudaSuccess) predict_tc_kernel<5><<<blocks, 128, kTcSmemBytes, st>>>(a, P, pred); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_infer(const float* P, const float* phi, int64_t n, uint8_t* pred,
+                             int sm_count, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  cudaError_t e = tc_configure(mlp_infer_tc_kernel);
+  if (e != cudaSuccess) return e;
+  mlp_infer_tc_kernel<<<tc_grid(n, sm_count), 128, kTcSmemBytes, s>>>(P, phi, n, pred);
+  return cudaGetLastError();
+}
+
+}  // namespace pic

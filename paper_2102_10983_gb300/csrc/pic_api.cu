@@ -48,6 +48,7 @@ struct pic_ctx {
   uint16_t* lag_j = nullptr;
   int64_t* dslot_i0 = nullptr;
   int32_t heavy_budget = 256;
+  double* work = nullptr;  // FP64 form with PIC_DIAG_WORK: per-particle work of E
   int32_t* pred_queue = nullptr;
   const pic_mlp* mlp = nullptr;
   int32_t predict_every = 1;
@@ -93,7 +94,7 @@ static void free_all(pic_ctx* c) {
   void* ptrs[] = {c->x, c->px, c->py, c->pz, c->cell, c->frac, c->fpx, c->fpy, c->fpz,
                   c->status, c->ringE, c->ringB, c->staging, c->wtab64, c->wtab32,
                   c->dstats, c->queue, c->qcount, c->pred, c->pred_queue, c->half,
-                  c->coef, c->lag_step, c->lag_j, c->dslot_i0};
+                  c->coef, c->lag_step, c->lag_j, c->dslot_i0, c->work};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -195,6 +196,8 @@ extern "C" int pic_create(const pic_params* prm, int64_t capacity, int64_t windo
     return fail(nullptr, PIC_EINVAL, "pic_create: the mixed form needs 2^-100 <= dt < 2^100%s");
   if (prm->schedule != PIC_SCHED_PLAIN && prm->precision != PIC_MIXED)
     return fail(nullptr, PIC_EINVAL, "pic_create: the binned schedules need PIC_MIXED%s");
+  if (prm->diagnostics != 0 && (prm->diagnostics != PIC_DIAG_WORK || prm->precision != PIC_FP64))
+    return fail(nullptr, PIC_EINVAL, "pic_create: PIC_DIAG_WORK is the only diagnostic (FP64 form)%s");
   if (capacity < 0 || capacity > ((int64_t)1 << 31) - 1)
     return fail(nullptr, PIC_EINVAL, "pic_create: capacity must be 0..2^31-1%s");
   if (!is_pow2(window_cells) || window_cells < 16 || window_cells > ((int64_t)1 << 30))
@@ -251,6 +254,7 @@ extern "C" int pic_create(const pic_params* prm, int64_t capacity, int64_t windo
     A((void**)&c->px, cap * 8);
     A((void**)&c->py, cap * 8);
     A((void**)&c->pz, cap * 8);
+    if (prm->diagnostics == PIC_DIAG_WORK) A((void**)&c->work, cap * 8);
   }
   A((void**)&c->status, cap);
   // the mixed form's ring is mirrored (2R slots, see PushArgsMixed)
@@ -368,6 +372,7 @@ extern "C" int pic_particles_write(pic_ctx* c, const double* x, const double* px
   else
     CUDA_TRY(c, cudaMemsetAsync(c->status, 0, (size_t)n, c->stream));
   if (c->prm.precision == PIC_FP64) {
+    if (c->work) CUDA_TRY(c, cudaMemsetAsync(c->work, 0, (size_t)n * 8, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->x, x, (size_t)n * 8, kind_in(where), c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->px, px, (size_t)n * 8, kind_in(where), c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->py, py, (size_t)n * 8, kind_in(where), c->stream));
@@ -497,6 +502,16 @@ static int collect_stats(pic_ctx* c, pic_step_stats* out, bool reset) {
   if (h.error) return fail(c, PIC_ETIMEOUT, "device error word set%s");
   if (out->out_of_window) return fail(c, PIC_ERANGE, "particles left the field window%s");
   if (out->clamped) return fail(c, PIC_EKMAX, "criterion capped at k_max%s");
+  return PIC_OK;
+}
+
+extern "C" int pic_work_read(pic_ctx* c, double* work, int64_t n, int32_t where) {
+  if (!c) return PIC_EINVAL;
+  if (!c->work) return fail(c, PIC_EINVAL, "pic_work_read: create the context with PIC_DIAG_WORK%s");
+  if (!work || n < 0 || n > c->n) return fail(c, PIC_EINVAL, "pic_work_read: bad buffer or count%s");
+  if (where != PIC_HOST && where != PIC_DEVICE) return fail(c, PIC_EINVAL, "bad where%s");
+  if (n > 0) CUDA_TRY(c, cudaMemcpyAsync(work, c->work, (size_t)n * 8, kind_out(where), c->stream));
+  if (where == PIC_HOST) CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return PIC_OK;
 }
 
@@ -649,6 +664,7 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
       a.wtab = c->wtab64;
       a.crit_row = wrows_total(c->prm.k_max) - 1;
       a.stats = c->dstats;
+      a.work = c->work;
       e = mark(ev0);
       if (e == cudaSuccess) e = launch_push_f64(a, p, c->stream, &launches);
     } else {

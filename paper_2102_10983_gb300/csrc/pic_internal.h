@@ -62,6 +62,7 @@ struct PushArgsF64 {
   const double* wtab;  // rows of [E weights p+1 | B weights p+1]
   int64_t crit_row;
   DevStats* stats;
+  double* work;  // nullptr, or per particle the accumulated work of E (App. B)
 };
 
 // Arguments of the mixed-precision push.  Position = (cell + frac) * dx with

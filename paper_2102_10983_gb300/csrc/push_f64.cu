@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(256) push_f64_kernel(PushArgsF64 a) {
 
     const double* wr = a.wtab + wrow(k, 1) * stride;
     bool frozen = false;
+    double work = a.work ? a.work[i] : 0.0;
     for (int64_t j = 1; j <= m; ++j, wr += stride) {
       s = xi * a.inv_dx;
       sb = s - 0.5;
@@ -146,6 +147,8 @@ __global__ void __launch_bounds__(256) push_f64_kernel(PushArgsF64 a) {
       const double ey = gather_f64<P>(E, wr, s, a.mask);
       const double bz = gather_f64<P>(B, wr + (P + 1), sb, a.mask);
       const double hp = (j == 1) ? 0.5 * (h_old + h) : h;
+      double vy_before = 0.0;
+      if (a.work) vy_before = pv1 / sqrt(1.0 + (pv0 * pv0 + pv1 * pv1 + pv2 * pv2));
       // Boris, E = (0, ey, 0), B = (0, 0, bz)
       const double half = 0.5 * hp;
       const double dpy = (a.qm * ey) * half;
@@ -161,8 +164,11 @@ __global__ void __launch_bounds__(256) push_f64_kernel(PushArgsF64 a) {
       pv1 = qy + dpy;
       pv2 = mz;
       const double g = sqrt(1.0 + (pv0 * pv0 + pv1 * pv1 + pv2 * pv2));
+      // the work of E over this push (App. B): (q hp / 2) E . (v_before + v_after)
+      if (a.work) work = work + ((a.qm * hp) * 0.5) * (ey * (vy_before + pv1 / g));
       xi = xi + h * (pv0 / g);
     }
+    if (a.work) a.work[i] = work;
     a.x[i] = xi;
     a.px[i] = pv0;
     a.py[i] = pv1;

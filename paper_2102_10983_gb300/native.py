@@ -19,6 +19,7 @@ PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA, PIC_ERANGE, PIC_EKMAX, PIC_ETIMEOUT =
 PIC_HOST, PIC_DEVICE = 0, 1
 PIC_FP64, PIC_MIXED = 0, 1
 PIC_SCHED_PLAIN, PIC_SCHED_BINNED, PIC_SCHED_PREDICTED = 0, 1, 2
+PIC_DIAG_WORK = 1
 PIC_STATUS_LOST = 0x80
 
 ERR_NAMES = {0: "PIC_OK", 1: "PIC_EINVAL", 2: "PIC_ENOMEM", 3: "PIC_ECUDA", 4: "PIC_ERANGE",
@@ -30,7 +31,7 @@ class PicParams(ctypes.Structure):
                 ("qm", ctypes.c_double), ("order", ctypes.c_int32), ("k_max", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("field_time", ctypes.c_int32),
                 ("schedule", ctypes.c_int32), ("heavy_budget", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("diagnostics", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class PicEnsemble(ctypes.Structure):
@@ -86,6 +87,7 @@ SIGNATURES = {
     "pic_timing_read": (ctypes.c_int, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_I64), _I32]),
     "pic_launch_count": (ctypes.c_int64, [_VP]),
     "pic_inject_error": (ctypes.c_int, [_VP, _I32]),
+    "pic_work_read": (ctypes.c_int, [_VP, _VP, _I64, _I32]),
     "pic_last_error": (ctypes.c_char_p, [_VP]),
     "pic_features": (ctypes.c_int, [_VP, _I64, _VP]),
     "pic_predict": (ctypes.c_int, [_VP, _VP, _I64, _VP]),
@@ -197,10 +199,10 @@ class Integrator:
 
     def __init__(self, dt, dx, psi_max, order=3, k_max=7, precision=PIC_FP64, field_time=0,
                  schedule=PIC_SCHED_PLAIN, qm=-1.0, capacity=0, window=256, ring_levels=None,
-                 stream=None, heavy_budget=0):
+                 stream=None, heavy_budget=0, diagnostics=0):
         self.params = PicParams(float(dt), float(dx), float(psi_max), float(qm), int(order),
                                 int(k_max), int(precision), int(field_time), int(schedule),
-                                int(heavy_budget))
+                                int(heavy_budget), int(diagnostics))
         self.window = int(window)
         self.ring_levels = int(ring_levels if ring_levels is not None else order + 1)
         self.capacity = int(capacity)
@@ -271,6 +273,13 @@ class Integrator:
 
     def launches(self) -> int:
         return int(lib().pic_launch_count(self.ctx))
+
+    def work_read(self, work=None):
+        """The per-particle work of E (PIC_DIAG_WORK contexts): numpy unless
+        a device tensor is given."""
+        out = np.empty(self.n) if work is None else work
+        _check(lib().pic_work_read(self.ctx, _ptr(out)[0], self.n, _where(out)), self.ctx)
+        return out
 
     def inject_error(self, word: int = 1):
         _check(lib().pic_inject_error(self.ctx, int(word)), self.ctx)

@@ -36,7 +36,7 @@ def run_oracle(wl: Workload, prm: oracle.Params, parts: oracle.Particles, n0: in
 
 def run_oracle_follow(wl: Workload, prm: oracle.Params, parts: oracle.Particles, n0: int,
                       n_steps: int, chunk: int = 48, margin: int = 6, r_ref=None, r_dev=None,
-                      stats=None, on_chunk=None) -> oracle.OrcStats:
+                      stats=None, on_chunk=None, work=None) -> oracle.OrcStats:
     """Like run_oracle, with a small window that follows the particles (all
     levels of a chunk share one origin; particles move < 1 node per step)."""
     p = prm.order
@@ -53,7 +53,7 @@ def run_oracle_follow(wl: Workload, prm: oracle.Params, parts: oracle.Particles,
         i0 = np.full(c + p, lo, dtype=np.int64)
         from paper_2102_10983_gb300.workloads import sample_levels
         E, B = sample_levels(wl.wave, wl.dt, wl.dx, n - p, c + p, i0, W, rowwise=False)
-        oracle.run(prm, parts, E, i0, B, i0, st, r_ref, r_dev)
+        oracle.run(prm, parts, E, i0, B, i0, st, r_ref, r_dev, work)
         done += c
         if on_chunk is not None:
             on_chunk(n + c, parts)

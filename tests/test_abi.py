@@ -52,6 +52,8 @@ def test_host_side_validation_rejects_bad_parameters():
         native.PicParams(0.1, 1.0, 0.01, -1.0, 3, 7, 2, 0, 0),     # precision
         native.PicParams(0.1, 1.0, -1.0, -1.0, 3, 7, 0, 0, 0),     # psi_max < 0
         native.PicParams(0.1, 1.0, 0.01, -1.0, 3, 7, 0, 0, 1),     # binned needs mixed
+        native.PicParams(0.1, 1.0, 0.01, -1.0, 3, 7, 1, 0, 0, 0, native.PIC_DIAG_WORK),  # FP64 only
+        native.PicParams(0.1, 1.0, 0.01, -1.0, 3, 7, 0, 0, 0, 0, 2),  # unknown diagnostic
     ]
     for prm in bad:
         assert L.pic_create(ctypes.byref(prm), 16, 64, 8, None, ctypes.byref(h)) == native.PIC_EINVAL
