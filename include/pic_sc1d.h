@@ -53,8 +53,8 @@ typedef struct {
   int32_t field_time; /* 0: sub-step fields at the position time t_n + (j-1)h;
                          1: the middle of the j-th sub-interval                  */
   int32_t n_cells;    /* N, 16 .. 2^26                                           */
-  int32_t gauss_every; /* pic_sc1d_step checks Gauss's law after every this many
-                          steps (0: never)                                       */
+  int32_t gauss_every; /* pic_sc1d_step checks Gauss's law after every macro
+                          step s with s + 1 a multiple of this (0: never)         */
   int32_t reserved[3];
 } pic_sc1d_params;
 
@@ -102,7 +102,7 @@ int pic_sc1d_fields_read(pic_sc1d* c, int64_t level, double* Ex, double* Ey, dou
                          int32_t where);
 
 /* Macro steps n0 .. n0 + n_steps - 1 (push, deposit, field solve; Gauss check
- * after every gauss_every-th step of the call).  Level n0 must be the newest
+ * after the steps s with s + 1 a multiple of gauss_every).  Level n0 must be the newest
  * stored.  With stats: synchronizes, returns and resets the counters and the
  * Gauss maxima accumulated since the last stats (PIC_EKMAX if k was capped).
  * Errors: PIC_EINVAL, PIC_ECUDA, PIC_EKMAX. */

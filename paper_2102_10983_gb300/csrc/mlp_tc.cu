@@ -4,11 +4,13 @@
 // exponent k the criterion of Sec. IV will pick next, for binning; the
 // criterion still decides every sub-step.
 //
-// Per CTA (128 threads, one warpgroup) and tile of 128 particles:
+// Per CTA (256 threads: two warpgroups, one tile of 128 particles each, so
+// every MMA round trip serves 256 particles):
 //   features: each thread forms one particle's phi (6 values, BF16, zero-
-//     padded to K = 16) and stores it as row r of A1 [128 x 16];
+//     padded to K = 16) and stores it as row r of its tile's A1 [128 x 16];
 //   layer 1: one tcgen05.mma M=128 N=64 K=16, A1 x W1^T -> D1 (TMEM cols 0..63);
-//   epilogue 1: each warp reads its 32 TMEM lanes (rows) with tcgen05.ld, adds
+//   epilogue 1: each warp reads its 32 TMEM lanes (rows; warp w of the CTA
+//     reads lanes 32 (w % 4) of tile w / 4's columns) with tcgen05.ld, adds
 //     b1, applies ReLU, rounds to BF16 and writes A2 [128 x 64];
 //   layer 2: four MMAs (K = 16 each) A2 x W2^T -> D2 (cols 64..127);
 //   epilogue 2: b2, ReLU, BF16 -> A2 again (layer 2 has read it);
@@ -33,23 +35,26 @@ namespace pic {
 namespace {
 
 constexpr int kTcRows = 128;  // particles per tile (MMA M)
+constexpr int kTcTiles = 2;   // tiles per CTA (one per warpgroup)
+constexpr int kTcThreads = kTcRows * kTcTiles;
 constexpr int kTcH = 64, kTcIn = 6, kTcOut = 8;
-constexpr uint32_t kTmemCols = 128;
+constexpr uint32_t kTileCols = 128;  // TMEM columns per tile: D1 / D3 at +0, D2 at +64
+constexpr uint32_t kTmemCols = kTileCols * kTcTiles;
 
 struct TcSmem {
   __align__(1024) unsigned char W1[kTcH * 16 * 2];    // [64 x 16]
   __align__(1024) unsigned char W2[kTcH * kTcH * 2];  // [64 x 64]
   __align__(1024) unsigned char W3[16 * kTcH * 2];    // [16 x 64], rows 8..15 zero
-  __align__(1024) unsigned char A1[kTcRows * 16 * 2];     // [128 x 16]
-  __align__(1024) unsigned char A2[kTcRows * kTcH * 2];   // [128 x 64]
+  __align__(1024) unsigned char A1[kTcTiles][kTcRows * 16 * 2];    // [128 x 16] per tile
+  __align__(1024) unsigned char A2[kTcTiles][kTcRows * kTcH * 2];  // [128 x 64] per tile
   float b1[kTcH], b2[kTcH], b3[kTcOut];
   __align__(8) uint64_t bar;
   uint32_t tmem;
   int failed;
 };
-// Reserved per CTA so that at most four CTAs share an SM: four 128-column
+// Reserved per CTA so that at most two CTAs share an SM: two 256-column
 // TMEM allocations fill its 512 columns, so an allocation never waits.
-constexpr size_t kTcSmemBytes = 48 * 1024;
+constexpr size_t kTcSmemBytes = 100 * 1024;
 static_assert(sizeof(TcSmem) + 1024 <= kTcSmemBytes, "tile buffers fit the reservation");
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -155,22 +160,22 @@ __device__ void tc_load_weights(TcSmem& s, const float* P) {
   if (threadIdx.x < kTcOut) s.b3[threadIdx.x] = b3[threadIdx.x];
 }
 
-// Row r of A1 from this thread's features (BF16, columns 6..15 zero).
-__device__ __forceinline__ void put_features(TcSmem& s, int r, const float (&f)[6]) {
+// Row r of tile q's A1 from this thread's features (BF16, columns 6..15 zero).
+__device__ __forceinline__ void put_features(TcSmem& s, int q, int r, const float (&f)[6]) {
   uint4 lo, hi;
   lo.x = bf2(f[0], f[1]);
   lo.y = bf2(f[2], f[3]);
   lo.z = bf2(f[4], f[5]);
   lo.w = 0u;
   hi = make_uint4(0u, 0u, 0u, 0u);
-  *reinterpret_cast<uint4*>(s.A1 + cm_off(r, 0, 16)) = lo;
-  *reinterpret_cast<uint4*>(s.A1 + cm_off(r, 8, 16)) = hi;
+  *reinterpret_cast<uint4*>(s.A1[q] + cm_off(r, 0, 16)) = lo;
+  *reinterpret_cast<uint4*>(s.A1[q] + cm_off(r, 8, 16)) = hi;
 }
 
 // Hidden layer epilogue: accumulator columns [c0, c0 + 64) of row r, plus
-// bias, ReLU, BF16, into row r of A2.
+// bias, ReLU, BF16, into row r of tile q's A2.
 __device__ __forceinline__ void hidden_epilogue(TcSmem& s, uint32_t lane_addr, int c0,
-                                                const float* bias, int r) {
+                                                const float* bias, int q, int r) {
 #pragma unroll
   for (int blk = 0; blk < 4; ++blk) {
     float v[16];
@@ -179,33 +184,38 @@ __device__ __forceinline__ void hidden_epilogue(TcSmem& s, uint32_t lane_addr, i
     for (int q = 0; q < 16; ++q) v[q] = fmaxf(v[q] + bias[16 * blk + q], 0.f);
     uint4 w0 = make_uint4(bf2(v[0], v[1]), bf2(v[2], v[3]), bf2(v[4], v[5]), bf2(v[6], v[7]));
     uint4 w1 = make_uint4(bf2(v[8], v[9]), bf2(v[10], v[11]), bf2(v[12], v[13]), bf2(v[14], v[15]));
-    *reinterpret_cast<uint4*>(s.A2 + cm_off(r, 16 * blk, kTcH)) = w0;
-    *reinterpret_cast<uint4*>(s.A2 + cm_off(r, 16 * blk + 8, kTcH)) = w1;
+    *reinterpret_cast<uint4*>(s.A2[q] + cm_off(r, 16 * blk, kTcH)) = w0;
+    *reinterpret_cast<uint4*>(s.A2[q] + cm_off(r, 16 * blk + 8, kTcH)) = w1;
   }
 }
 
-// The network on the tile whose row r (this thread) carries features f;
-// returns the class (argmax, ties to the smaller k) or 0xFF after a give-up.
+// The network on the CTA's two tiles; this thread carries the features f of
+// row r of tile q (thread t: q = t / 128, r = t % 128), which is also the row
+// its warp reads back (warp w: TMEM lanes 32 (w % 4) .. + 31 of tile w / 4).
+// Returns the class (argmax, ties to the smaller k) or 0xFF after a give-up.
 // Collective over the CTA.  `ph` is the mbarrier phase, advanced per commit.
-__device__ __forceinline__ int tc_tile(TcSmem& s, const float (&f)[6], uint32_t& ph) {
-  const int r = threadIdx.x;
+__device__ __forceinline__ int tc_tiles(TcSmem& s, const float (&f)[6], uint32_t& ph) {
+  const int q = threadIdx.x >> 7, r = threadIdx.x & 127;
   const int warp = threadIdx.x >> 5;
-  put_features(s, r, f);
+  put_features(s, q, r, f);
   fence_async_smem();
   fence_before();
   __syncthreads();
   fence_after();
-  const uint32_t lane_addr = s.tmem + ((uint32_t)(32 * warp) << 16);
+  const uint32_t col0 = kTileCols * (uint32_t)q;
+  const uint32_t lane_addr = s.tmem + ((uint32_t)(32 * (warp & 3)) << 16) + col0;
   bool ok = !s.failed;
   // layer 1
   if (ok && threadIdx.x == 0) {
-    mma_bf16(s.tmem, sdesc(saddr(s.A1), 128, 256), sdesc(saddr(s.W1), 128, 256),
-             idesc_bf16(kTcRows, kTcH), 0);
+#pragma unroll
+    for (int t = 0; t < kTcTiles; ++t)
+      mma_bf16(s.tmem + kTileCols * t, sdesc(saddr(s.A1[t]), 128, 256), sdesc(saddr(s.W1), 128, 256),
+               idesc_bf16(kTcRows, kTcH), 0);
     mma_commit(&s.bar);
   }
   if (ok) { ok = bar_wait(&s.bar, ph); ph ^= 1u; }
   fence_after();
-  if (ok) hidden_epilogue(s, lane_addr, 0, s.b1, r);
+  if (ok) hidden_epilogue(s, lane_addr, 0, s.b1, q, r);
   fence_async_smem();
   fence_before();
   if (!ok) s.failed = 1;
@@ -215,14 +225,16 @@ __device__ __forceinline__ int tc_tile(TcSmem& s, const float (&f)[6], uint32_t&
   // layer 2
   if (ok && threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-      mma_bf16(s.tmem + kTcH, sdesc(saddr(s.A2) + 256u * k, 128, 1024),
-               sdesc(saddr(s.W2) + 256u * k, 128, 1024), idesc_bf16(kTcRows, kTcH), k > 0);
+    for (int t = 0; t < kTcTiles; ++t)
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        mma_bf16(s.tmem + kTileCols * t + kTcH, sdesc(saddr(s.A2[t]) + 256u * k, 128, 1024),
+                 sdesc(saddr(s.W2) + 256u * k, 128, 1024), idesc_bf16(kTcRows, kTcH), k > 0);
     mma_commit(&s.bar);
   }
   if (ok) { ok = bar_wait(&s.bar, ph); ph ^= 1u; }
   fence_after();
-  if (ok) hidden_epilogue(s, lane_addr, kTcH, s.b2, r);
+  if (ok) hidden_epilogue(s, lane_addr, kTcH, s.b2, q, r);
   fence_async_smem();
   fence_before();
   if (!ok) s.failed = 1;
@@ -232,9 +244,11 @@ __device__ __forceinline__ int tc_tile(TcSmem& s, const float (&f)[6], uint32_t&
   // layer 3
   if (ok && threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-      mma_bf16(s.tmem, sdesc(saddr(s.A2) + 256u * k, 128, 1024),
-               sdesc(saddr(s.W3) + 256u * k, 128, 1024), idesc_bf16(kTcRows, 16), k > 0);
+    for (int t = 0; t < kTcTiles; ++t)
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        mma_bf16(s.tmem + kTileCols * t, sdesc(saddr(s.A2[t]) + 256u * k, 128, 1024),
+                 sdesc(saddr(s.W3) + 256u * k, 128, 1024), idesc_bf16(kTcRows, 16), k > 0);
     mma_commit(&s.bar);
   }
   if (ok) { ok = bar_wait(&s.bar, ph); ph ^= 1u; }
@@ -253,7 +267,7 @@ __device__ __forceinline__ int tc_tile(TcSmem& s, const float (&f)[6], uint32_t&
   }
   fence_before();
   if (!ok) s.failed = 1;
-  __syncthreads();  // A1, A2 and the TMEM columns are reused by the next tile
+  __syncthreads();  // A1, A2 and the TMEM columns are reused by the next tiles
   fence_after();
   return s.failed ? 0xFF : cls;
 }
@@ -289,7 +303,7 @@ __device__ __forceinline__ void tc_end(TcSmem& s) {
 // pic_predict: features of every particle after step a's levels (theta = 3/2,
 // the same code as the features kernel) and the network's class, in one pass.
 template <int P>
-__global__ void __launch_bounds__(128) predict_tc_kernel(PushArgsMixed a, const float* Pm, uint8_t* pred) {
+__global__ void __launch_bounds__(kTcThreads) predict_tc_kernel(PushArgsMixed a, const float* Pm, uint8_t* pred) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   TcSmem& s = *reinterpret_cast<TcSmem*>(smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023));
   tc_begin(s, Pm);
@@ -298,12 +312,12 @@ __global__ void __launch_bounds__(128) predict_tc_kernel(PushArgsMixed a, const 
   float w[2 * (P + 1)];
   lagrange_f32<P>(1.5f, w);
   uint32_t ph = 0;
-  const int64_t n_tiles = (a.n + kTcRows - 1) / kTcRows;
-  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-    const int64_t i = t * kTcRows + threadIdx.x;
+  const int64_t n_groups = (a.n + kTcThreads - 1) / kTcThreads;
+  for (int64_t t = blockIdx.x; t < n_groups; t += gridDim.x) {
+    const int64_t i = t * kTcThreads + threadIdx.x;
     float f[6];
     particle_features<P>(a, F, w, i, f);
-    const int c = tc_tile(s, f, ph);
+    const int c = tc_tiles(s, f, ph);
     if (i < a.n) pred[i] = (uint8_t)c;
     if (s.failed) break;
   }
@@ -312,21 +326,21 @@ __global__ void __launch_bounds__(128) predict_tc_kernel(PushArgsMixed a, const 
 }
 
 // pic_mlp_infer: the network's class of n feature rows phi[n][6].
-__global__ void __launch_bounds__(128) mlp_infer_tc_kernel(const float* Pm, const float* phi, int64_t n,
-                                                           uint8_t* pred) {
+__global__ void __launch_bounds__(kTcThreads) mlp_infer_tc_kernel(const float* Pm, const float* phi,
+                                                                  int64_t n, uint8_t* pred) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   TcSmem& s = *reinterpret_cast<TcSmem*>(smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023));
   tc_begin(s, Pm);
   uint32_t ph = 0;
-  const int64_t n_tiles = (n + kTcRows - 1) / kTcRows;
-  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-    const int64_t i = t * kTcRows + threadIdx.x;
+  const int64_t n_groups = (n + kTcThreads - 1) / kTcThreads;
+  for (int64_t t = blockIdx.x; t < n_groups; t += gridDim.x) {
+    const int64_t i = t * kTcThreads + threadIdx.x;
     float f[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (i < n) {
 #pragma unroll
       for (int q = 0; q < 6; ++q) f[q] = phi[i * 6 + q];
     }
-    const int c = tc_tile(s, f, ph);
+    const int c = tc_tiles(s, f, ph);
     if (i < n) pred[i] = (uint8_t)c;
     if (s.failed) break;
   }
@@ -334,9 +348,9 @@ __global__ void __launch_bounds__(128) mlp_infer_tc_kernel(const float* Pm, cons
 }
 
 static int tc_grid(int64_t n, int sm_count) {
-  const int64_t tiles = (n + kTcRows - 1) / kTcRows;
-  const int64_t cap = (int64_t)(sm_count > 0 ? sm_count : 152) * 4;
-  return (int)(tiles < cap ? tiles : cap);
+  const int64_t groups = (n + kTcThreads - 1) / kTcThreads;
+  const int64_t cap = (int64_t)(sm_count > 0 ? sm_count : 152) * 2;
+  return (int)(groups < cap ? groups : cap);
 }
 
 template <class K>
@@ -350,11 +364,11 @@ cudaError_t launch_predict_fused(const PushArgsMixed& a, int order, const float*
   const int blocks = tc_grid(a.n, sm_count);
   cudaError_t e = cudaSuccess;
   switch (order) {
-    case 1: e = tc_configure(predict_tc_kernel<1>); if (e == cudaSuccess) predict_tc_kernel<1><<<blocks, 128, kTcSmemBytes, st>>>(a, P, pred); break;
-    case 2: e = tc_configure(predict_tc_kernel<2>); if (e == cudaSuccess) predict_tc_kernel<2><<<blocks, 128, kTcSmemBytes, st>>>(a, P, pred); break;
-    case 3: e = tc_configure(predict_tc_kernel<3>); if (e == cudaSuccess) predict_tc_kernel<3><<<blocks, 128, kTcSmemBytes, st>>>(a, P, pred); break;
-    case 4: e = tc_configure(predict_tc_kernel<4>); if (e == cudaSuccess) predict_tc_kernel<4><<<blocks, 128, kTcSmemBytes, st>>>(a, P, pred); break;
-    case 5: e = tc_configure(predict_tc_kernel<5>); if (e == cudaSuccess) predict_tc_kernel<5><<<blocks, 128, kTcSmemBytes, st>>>(a, P, pred); break;
+    case 1: e = tc_configure(predict_tc_kernel<1>); if (e == cudaSuccess) predict_tc_kernel<1><<<blocks, kTcThreads, kTcSmemBytes, st>>>(a, P, pred); break;
+    case 2: e = tc_configure(predict_tc_kernel<2>); if (e == cudaSuccess) predict_tc_kernel<2><<<blocks, kTcThreads, kTcSmemBytes, st>>>(a, P, pred); break;
+    case 3: e = tc_configure(predict_tc_kernel<3>); if (e == cudaSuccess) predict_tc_kernel<3><<<blocks, kTcThreads, kTcSmemBytes, st>>>(a, P, pred); break;
+    case 4: e = tc_configure(predict_tc_kernel<4>); if (e == cudaSuccess) predict_tc_kernel<4><<<blocks, kTcThreads, kTcSmemBytes, st>>>(a, P, pred); break;
+    case 5: e = tc_configure(predict_tc_kernel<5>); if (e == cudaSuccess) predict_tc_kernel<5><<<blocks, kTcThreads, kTcSmemBytes, st>>>(a, P, pred); break;
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;
@@ -366,7 +380,7 @@ cudaError_t launch_mlp_infer(const float* P, const float* phi, int64_t n, uint8_
   if (n <= 0) return cudaSuccess;
   cudaError_t e = tc_configure(mlp_infer_tc_kernel);
   if (e != cudaSuccess) return e;
-  mlp_infer_tc_kernel<<<tc_grid(n, sm_count), 128, kTcSmemBytes, s>>>(P, phi, n, pred);
+  mlp_infer_tc_kernel<<<tc_grid(n, sm_count), kTcThreads, kTcSmemBytes, s>>>(P, phi, n, pred);
   return cudaGetLastError();
 }
 

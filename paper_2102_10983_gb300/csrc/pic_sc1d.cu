@@ -589,7 +589,7 @@ extern "C" int pic_sc1d_step(pic_sc1d* c, int64_t n0, int64_t n_steps, pic_sc1d_
     SC_TRY(c, cudaGetLastError());
     c->slot_level[s1] = s + 1;
     const int ge = c->prm.gauss_every;
-    if (ge > 0 && (j + 1) % ge == 0) {
+    if (ge > 0 && (((s + 1) % ge) + ge) % ge == 0) {  // after steps s + 1 = multiples of ge
       int rc = sc_gauss(c);
       if (rc != PIC_OK) return rc;
       gauss_kernel<<<grid_for(c, c->M), 256, 0, c->stream>>>(slot_field(c, s1, 0), accC(c), accCion(c),
