@@ -4,18 +4,21 @@
 // exponent k the criterion of Sec. IV will pick next, for binning; the
 // criterion still decides every sub-step.
 //
-// Per CTA (256 threads: two warpgroups, one tile of 128 particles each, so
-// every MMA round trip serves 256 particles):
+// Per CTA (128 threads, one warpgroup) and tile of 128 particles:
 //   features: each thread forms one particle's phi (6 values, BF16, zero-
-//     padded to K = 16) and stores it as row r of its tile's A1 [128 x 16];
+//     padded to K = 16) and stores it as row r of A1 [128 x 16];
 //   layer 1: one tcgen05.mma M=128 N=64 K=16, A1 x W1^T -> D1 (TMEM cols 0..63);
-//   epilogue 1: each warp reads its 32 TMEM lanes (rows; warp w of the CTA
-//     reads lanes 32 (w % 4) of tile w / 4's columns) with tcgen05.ld, adds
+//   epilogue 1: each warp reads its 32 TMEM lanes (rows) with tcgen05.ld, adds
 //     b1, applies ReLU, rounds to BF16 and writes A2 [128 x 64];
-//   layer 2: four MMAs (K = 16 each) A2 x W2^T -> D2 (cols 64..127);
+//   layer 2: four MMAs (K = 16 each) A2 x W2^T -> D2, in the same columns (the
+//     epilogue has read D1);
 //   epilogue 2: b2, ReLU, BF16 -> A2 again (layer 2 has read it);
 //   layer 3: four MMAs A2 x W3^T (N = 16, rows 8..15 of W3 zero) -> D3 (cols 0..15);
 //   epilogue 3: b3, argmax over the 8 classes (ties: the smaller k).
+// A CTA holds 64 TMEM columns and ~33 KB of shared memory, so six CTAs (24
+// warps, six tiles in flight) share an SM: the chain of a tile (features,
+// three MMA round trips, three epilogues) is latency-bound, the SM is kept
+// busy by the other tiles.
 // One thread issues the MMAs and commits them to an mbarrier that every
 // thread waits on (a bounded wait: on a give-up the CTA records it, marks its
 // remaining predictions 0xFF, an invalid class, frees its TMEM and returns).
@@ -35,10 +38,10 @@ namespace pic {
 namespace {
 
 constexpr int kTcRows = 128;  // particles per tile (MMA M)
-constexpr int kTcTiles = 2;   // tiles per CTA (one per warpgroup)
+constexpr int kTcTiles = 1;   // tiles per CTA
 constexpr int kTcThreads = kTcRows * kTcTiles;
 constexpr int kTcH = 64, kTcIn = 6, kTcOut = 8;
-constexpr uint32_t kTileCols = 128;  // TMEM columns per tile: D1 / D3 at +0, D2 at +64
+constexpr uint32_t kTileCols = 64;  // TMEM columns per tile: D1, then D2, then D3
 constexpr uint32_t kTmemCols = kTileCols * kTcTiles;
 
 struct TcSmem {
@@ -52,9 +55,9 @@ struct TcSmem {
   uint32_t tmem;
   int failed;
 };
-// Reserved per CTA so that at most two CTAs share an SM: two 256-column
-// TMEM allocations fill its 512 columns, so an allocation never waits.
-constexpr size_t kTcSmemBytes = 100 * 1024;
+// Reserved per CTA so that at most six CTAs share an SM: six 64-column TMEM
+// allocations fit its 512 columns, so an allocation never waits.
+constexpr size_t kTcSmemBytes = 37 * 1024;
 static_assert(sizeof(TcSmem) + 1024 <= kTcSmemBytes, "tile buffers fit the reservation");
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -228,13 +231,13 @@ __device__ __forceinline__ int tc_tiles(TcSmem& s, const float (&f)[6], uint32_t
     for (int t = 0; t < kTcTiles; ++t)
 #pragma unroll
       for (int k = 0; k < 4; ++k)
-        mma_bf16(s.tmem + kTileCols * t + kTcH, sdesc(saddr(s.A2[t]) + 256u * k, 128, 1024),
+        mma_bf16(s.tmem + kTileCols * t, sdesc(saddr(s.A2[t]) + 256u * k, 128, 1024),
                  sdesc(saddr(s.W2) + 256u * k, 128, 1024), idesc_bf16(kTcRows, kTcH), k > 0);
     mma_commit(&s.bar);
   }
   if (ok) { ok = bar_wait(&s.bar, ph); ph ^= 1u; }
   fence_after();
-  if (ok) hidden_epilogue(s, lane_addr, kTcH, s.b2, q, r);
+  if (ok) hidden_epilogue(s, lane_addr, 0, s.b2, q, r);
   fence_async_smem();
   fence_before();
   if (!ok) s.failed = 1;
@@ -300,23 +303,20 @@ __device__ __forceinline__ void tc_end(TcSmem& s) {
 
 }  // namespace
 
-// pic_predict: features of every particle after step a's levels (theta = 3/2,
-// the same code as the features kernel) and the network's class, in one pass.
+// pic_predict: features of every particle after step a (a.halfE / a.halfB: its
+// feature nodes; the same code as the features kernel) and the network's
+// class, in one pass.
 template <int P>
 __global__ void __launch_bounds__(kTcThreads) predict_tc_kernel(PushArgsMixed a, const float* Pm, uint8_t* pred) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   TcSmem& s = *reinterpret_cast<TcSmem*>(smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023));
   tc_begin(s, Pm);
-  StepFields<P, true> F;
-  load_fields<P, true>(F, a, false);
-  float w[2 * (P + 1)];
-  lagrange_f32<P>(1.5f, w);
   uint32_t ph = 0;
   const int64_t n_groups = (a.n + kTcThreads - 1) / kTcThreads;
   for (int64_t t = blockIdx.x; t < n_groups; t += gridDim.x) {
     const int64_t i = t * kTcThreads + threadIdx.x;
     float f[6];
-    particle_features<P>(a, F, w, i, f);
+    particle_features(a, a.halfE, a.halfB, a.lo, a.hi, i, f);
     const int c = tc_tiles(s, f, ph);
     if (i < a.n) pred[i] = (uint8_t)c;
     if (s.failed) break;
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(kTcThreads) mlp_infer_tc_kernel(const float* P
 
 static int tc_grid(int64_t n, int sm_count) {
   const int64_t groups = (n + kTcThreads - 1) / kTcThreads;
-  const int64_t cap = (int64_t)(sm_count > 0 ? sm_count : 152) * 2;
+  const int64_t cap = (int64_t)(sm_count > 0 ? sm_count : 152) * 6;
   return (int)(groups < cap ? groups : cap);
 }
 

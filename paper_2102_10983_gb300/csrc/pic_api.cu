@@ -42,6 +42,7 @@ struct pic_ctx {
   uint8_t* pred = nullptr;
   float* half = nullptr;  // mixed form: E_y, B_z of every window node at the step's t_n
   float* coef = nullptr;  // mixed form: per node monomial coefficients, two steps (parity of s)
+  float* feat = nullptr;  // mixed form: the predictor's feature nodes (E_y, B_z at t_{n+1}), W + 1 each
   // binned mixed form: resumable long sub-cycles (per particle: the step it is
   // in and the sub-steps done), and a device copy of slot_i0 for the kernel
   int32_t* lag_step = nullptr;
@@ -94,7 +95,7 @@ static void free_all(pic_ctx* c) {
   void* ptrs[] = {c->x, c->px, c->py, c->pz, c->cell, c->frac, c->fpx, c->fpy, c->fpz,
                   c->status, c->ringE, c->ringB, c->staging, c->wtab64, c->wtab32,
                   c->dstats, c->queue, c->qcount, c->pred, c->pred_queue, c->half,
-                  c->coef, c->lag_step, c->lag_j, c->dslot_i0, c->work};
+                  c->coef, c->lag_step, c->lag_j, c->dslot_i0, c->work, c->feat};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -232,6 +233,7 @@ extern "C" int pic_create(const pic_params* prm, int64_t capacity, int64_t windo
   if (mixed) {
     A((void**)&c->half, 2 * ((size_t)window_cells + 1) * 4);  // E_y, B_z: W + 1 nodes each
     A((void**)&c->coef, 2 * (size_t)window_cells * 2 * (prm->order + 1) * 4);
+    A((void**)&c->feat, 2 * ((size_t)window_cells + 1) * 4);
     A((void**)&c->cell, cap * 4);
     A((void**)&c->frac, cap * 4);
     A((void**)&c->fpx, cap * 4);
@@ -714,8 +716,13 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
             PushArgsMixed fa = a;
             fill_mixed(c, fa, s - 1, plo, phi, false);
             fa.coef = fa.coef_p = nullptr;
-            e = launch_predict_fused(fa, p, mlp_device_params(c->mlp), c->pred, c->sm_count,
-                                     c->stream);
+            fa.halfE = c->feat;
+            fa.halfB = c->feat + W + 1;
+            e = launch_feature_nodes(fa, p, W, c->feat, c->feat + W + 1, c->stream);
+            ++launches;
+            if (e == cudaSuccess)
+              e = launch_predict_fused(fa, p, mlp_device_params(c->mlp), c->pred, c->sm_count,
+                                       c->stream);
             ++launches;
             if (e == cudaSuccess)
               e = launch_bin_predicted(c->pred, c->status, c->n, a.parity_cur, kPredMinK,
@@ -773,8 +780,11 @@ extern "C" int pic_features(pic_ctx* c, int64_t n, float* phi) {
   a.status = c->status;
   a.mask = (int32_t)(c->W - 1);
   fill_mixed(c, a, n, lo, hi, false);
+  a.halfE = c->feat;
+  a.halfB = c->feat + c->W + 1;
+  CUDA_TRY(c, launch_feature_nodes(a, c->prm.order, c->W, c->feat, c->feat + c->W + 1, c->stream));
   CUDA_TRY(c, launch_features_mixed(a, c->prm.order, phi, c->stream));
-  ++c->launches;
+  c->launches += 2;
   return PIC_OK;
 }
 
@@ -792,9 +802,12 @@ extern "C" int pic_predict(pic_ctx* c, const pic_mlp* mlp, int64_t n, uint8_t* p
   a.status = c->status;
   a.mask = (int32_t)(c->W - 1);
   fill_mixed(c, a, n, lo, hi, false);
+  a.halfE = c->feat;
+  a.halfB = c->feat + c->W + 1;
+  CUDA_TRY(c, launch_feature_nodes(a, c->prm.order, c->W, c->feat, c->feat + c->W + 1, c->stream));
   CUDA_TRY(c, launch_predict_fused(a, c->prm.order, mlp_device_params(mlp), pred, c->sm_count,
                                    c->stream));
-  ++c->launches;
+  c->launches += 2;
   return PIC_OK;
 }
 

@@ -214,6 +214,11 @@ cudaError_t launch_binned_step(const PushArgsMixed& a, int order, int sm_count, 
 // and (coef != nullptr) every node's monomial coefficients, 2(p+1) floats.
 cudaError_t launch_halfstep(const PushArgsMixed& a, int order, int64_t W, float* outE, float* outB,
                             float* coef, cudaStream_t s);
+// E_y, B_z of every window node extrapolated to t_{n+1} (theta = 3/2) from step
+// a's levels, W + 1 nodes each: the predictor's field features.
+cudaError_t launch_feature_nodes(const PushArgsMixed& a, int order, int64_t W, float* outE,
+                                 float* outB, cudaStream_t s);
+// Features of every particle (a.halfE / a.halfB: the feature nodes of a's step).
 cudaError_t launch_features_mixed(const PushArgsMixed& a, int order, float* phi, cudaStream_t s);
 
 // Rebuilds the predicted queue: clears the old queue's marks, then bins and
@@ -228,8 +233,9 @@ const float* mlp_device_params(const struct ::pic_mlp* m);
 int mlp_param_count();
 cudaError_t launch_mlp_infer(const float* P, const float* phi, int64_t n, uint8_t* pred,
                              int sm_count, cudaStream_t s);
-// Features of step a's levels (theta = 3/2) and the predicted class of every
-// particle in one pass (same predictions as features + launch_mlp_infer).
+// Features of step a's levels (theta = 3/2; a.halfE / a.halfB: the feature
+// nodes) and the predicted class of every particle in one pass (the same
+// predictions as features + launch_mlp_infer).
 cudaError_t launch_predict_fused(const PushArgsMixed& a, int order, const float* P, uint8_t* pred,
                                  int sm_count, cudaStream_t s);
 cudaError_t launch_mlp_grad(const float* P, const float* phi, const uint8_t* label, int64_t n,

@@ -672,12 +672,16 @@ __device__ __forceinline__ void load_fields(StepFields<P, RING>& F, const PushAr
 
 // phi = (asinh|E|, asinh|B|, asinh p_x, asinh p_y, asinh p_z, log gamma) of
 // particle i after macro step n, with E and B at its position extrapolated to
-// t_{n+1} (theta = 3/2, weights w) from step n's levels F: everything known
-// before level n+1 arrives.  Lost particles and i >= n get zeros; E and B are
-// zero outside the window.
-template <int P>
-__device__ __forceinline__ void particle_features(const PushArgsMixed& a, const StepFields<P, true>& F,
-                                                  const float* w, int64_t i, float (&f)[6]) {
+// t_{n+1} (theta = 3/2) from step n's levels: everything known before level
+// n+1 arrives.  The temporal extrapolation of every window node is done once
+// (feature_nodes_kernel: nodeE, nodeB, W + 1 nodes each, node W repeating
+// node 0), so a particle reads two nodes per grid and applies its tent weight:
+// the same operations, in the same order, as gathering the levels at the
+// particle.  lo, hi: step n's window.  Lost particles and i >= n get zeros;
+// E and B are zero outside the window.
+__device__ __forceinline__ void particle_features(const PushArgsMixed& a, const float* nodeE,
+                                                  const float* nodeB, int32_t lo, int32_t hi,
+                                                  int64_t i, float (&f)[6]) {
 #pragma unroll
   for (int q = 0; q < 6; ++q) f[q] = 0.f;
   if (i >= a.n) return;
@@ -686,11 +690,12 @@ __device__ __forceinline__ void particle_features(const PushArgsMixed& a, const 
   const MixedState s = load_state(a, i);
   int32_t je, jb;
   float we, wb;
-  if (tent_coords(s.cell, s.frac, F.lo, F.hi, je, we, jb, wb)) {
-    const float ey = gather_f32<P>(F.E, w, je, we, a.mask);
-    const float bz = gather_f32<P>(F.B, w + (P + 1), jb, wb, a.mask);
-    f[0] = asinhf(fabsf(ey));
-    f[1] = asinhf(fabsf(bz));
+  if (tent_coords(s.cell, s.frac, lo, hi, je, we, jb, wb)) {
+    const float* e = nodeE + (je & a.mask);
+    const float* b = nodeB + (jb & a.mask);
+    const float e0 = __ldg(e), e1 = __ldg(e + 1), b0 = __ldg(b), b1 = __ldg(b + 1);
+    f[0] = asinhf(fabsf(__fmaf_rn(we, __fsub_rn(e1, e0), e0)));
+    f[1] = asinhf(fabsf(__fmaf_rn(wb, __fsub_rn(b1, b0), b0)));
   }
   f[2] = asinhf(s.ux);
   f[3] = asinhf(s.uy);

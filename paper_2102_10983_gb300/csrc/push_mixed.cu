@@ -760,34 +760,66 @@ __global__ void reset_status_kernel(uint8_t* status, int64_t n) {
 
 // ---------------------------------------------------------------- predictor features
 
-// phi of every particle after macro step n (see particle_features).
+// Every window node's E_y and B_z extrapolated to t_{n+1} (theta = 3/2) from
+// step n's levels a: the temporal sum gather_f32 takes at a node, over the same
+// levels in the same order; W + 1 nodes each, node W repeating node 0.
 template <int P>
-__global__ void features_kernel(PushArgsMixed a, float* phi) {
+__global__ void feature_nodes_kernel(PushArgsMixed a, int64_t W, float* outE, float* outB) {
   StepFields<P, true> F;
   load_fields<P, true>(F, a, false);
   float w[2 * (P + 1)];
   lagrange_f32<P>(1.5f, w);
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < W;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    float fe = __fmul_rn(w[0], __ldg(F.E.at(0) + c));
+    float fb = __fmul_rn(w[P + 1], __ldg(F.B.at(0) + c));
+#pragma unroll
+    for (int l = 1; l <= P; ++l) {
+      fe = __fmaf_rn(w[l], __ldg(F.E.at(l) + c), fe);
+      fb = __fmaf_rn(w[P + 1 + l], __ldg(F.B.at(l) + c), fb);
+    }
+    outE[c] = fe;
+    outB[c] = fb;
+    if (c == 0) {
+      outE[W] = fe;
+      outB[W] = fb;
+    }
+  }
+}
+
+cudaError_t launch_feature_nodes(const PushArgsMixed& a, int order, int64_t W, float* outE,
+                                 float* outB, cudaStream_t s) {
+  const int64_t want = (W + 255) / 256;
+  const int blocks = (int)(want < 152 * 8 ? want : 152 * 8);
+  switch (order) {
+    case 1: feature_nodes_kernel<1><<<blocks, 256, 0, s>>>(a, W, outE, outB); break;
+    case 2: feature_nodes_kernel<2><<<blocks, 256, 0, s>>>(a, W, outE, outB); break;
+    case 3: feature_nodes_kernel<3><<<blocks, 256, 0, s>>>(a, W, outE, outB); break;
+    case 4: feature_nodes_kernel<4><<<blocks, 256, 0, s>>>(a, W, outE, outB); break;
+    case 5: feature_nodes_kernel<5><<<blocks, 256, 0, s>>>(a, W, outE, outB); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// phi of every particle after macro step n (see particle_features; a.halfE,
+// a.halfB: the feature nodes of step n).
+__global__ void features_kernel(PushArgsMixed a, float* phi) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n;
        i += (int64_t)gridDim.x * blockDim.x) {
     float f[6];
-    particle_features<P>(a, F, w, i, f);
+    particle_features(a, a.halfE, a.halfB, a.lo, a.hi, i, f);
 #pragma unroll
     for (int q = 0; q < 6; ++q) phi[i * 6 + q] = f[q];
   }
 }
 
 cudaError_t launch_features_mixed(const PushArgsMixed& a, int order, float* phi, cudaStream_t s) {
+  (void)order;
   if (a.n <= 0) return cudaSuccess;
   const int64_t want = (a.n + 255) / 256;
   const int blocks = (int)(want < 152 * 16 ? want : 152 * 16);
-  switch (order) {
-    case 1: features_kernel<1><<<blocks, 256, 0, s>>>(a, phi); break;
-    case 2: features_kernel<2><<<blocks, 256, 0, s>>>(a, phi); break;
-    case 3: features_kernel<3><<<blocks, 256, 0, s>>>(a, phi); break;
-    case 4: features_kernel<4><<<blocks, 256, 0, s>>>(a, phi); break;
-    case 5: features_kernel<5><<<blocks, 256, 0, s>>>(a, phi); break;
-    default: return cudaErrorInvalidValue;
-  }
+  features_kernel<<<blocks, 256, 0, s>>>(a, phi);
   return cudaGetLastError();
 }
 

@@ -260,7 +260,7 @@ def test_mixed_within_budget_front_passage(order):
     E, B, i0 = wl.levels(-p, 2500 + p)
     ini = wl.particles()
     init = [torch.as_tensor(a, device="cuda") for a in (ini.x, ini.px, ini.py, ini.pz)]
-    u = accuracy.BACKWARD_ULPS
+    u = accuracy.BACKWARD_ULPS_BY_ORDER[order]
     res = accuracy.front_accuracy(native, wl, init, 2500, E, B, i0, 2500 + p + 1,
                                   torch.cuda.current_stream(), native.PIC_SCHED_PLAIN,
                                   unresolved=True, ulps=(u,))
