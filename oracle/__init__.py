@@ -25,7 +25,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pic_oracle.c")
-_SRCS = [_SRC, os.path.join(_HERE, "pic1d_oracle.c")]
+_SRCS = [_SRC, os.path.join(_HERE, "pic1d_oracle.c"), os.path.join(_HERE, "traj_oracle.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liborc.so")
 _lib = None

@@ -1,0 +1,103 @@
+"""The single-electron studies of Secs. IV-VII with the oracle (oracle/study.py):
+one electron from rest through the Gaussian-enveloped wave (sigma = 8 pi),
+c dt/dx = 0.99, Psi_max = 0.01 where sub-cycling, the field sampled on the
+grid.  Each test states the paper's claim it checks; the scans use
+a0 in {10, 25, 50, 100} (the paper: 5 <= a0 <= 100).
+"""
+from __future__ import annotations
+
+import pytest
+
+from oracle import study
+
+A0S = (10.0, 25.0, 50.0, 100.0)
+NOSUB = 1e30
+
+
+@pytest.fixture(scope="module")
+def scan():
+    keys = [(a0, o, ps, res) for a0 in A0S
+            for (o, ps, res) in ((1, NOSUB, 75), (1, 0.01, 75), (3, 0.01, 75), (3, NOSUB, 75),
+                                 (5, 0.01, 75), (5, NOSUB, 75), (1, NOSUB, 600),
+                                 (1, 0.01, 150), (3, 0.01, 150), (1, 0.01, 300), (3, 0.01, 300))]
+    res = study.run([study.params(a0, o, ps, r) for a0, o, ps, r in keys])
+    return dict(zip(keys, res))
+
+
+def eps(scan, a0, o, ps, res, what="eps_dephasing"):
+    return scan[(a0, o, ps, res)][what]
+
+
+def test_third_order_with_subcycling_keeps_dephasing_below_a_tenth(scan):
+    """Sec. VII: order 3 + sub-cycling at lambda/75 keeps eps_dephasing < 0.1
+    over the a0 scan."""
+    for a0 in A0S:
+        assert eps(scan, a0, 3, 0.01, 75) < 0.1, a0
+
+
+def test_standard_pic_degrades_with_a0_and_underestimates_the_energy(scan):
+    """Sec. IV: the standard algorithm (order 1, no sub-cycling) at lambda/75
+    grows in error with a0, is significant above a0 ~ 40, and at a0 = 100
+    reaches about a third of the theoretical peak energy."""
+    e = [eps(scan, a0, 1, NOSUB, 75) for a0 in A0S]
+    assert all(b > a for a, b in zip(e, e[1:])), e
+    assert e[0] < 0.1 < 1.0 < e[2]
+    g_ratio = scan[(100.0, 1, NOSUB, 75)]["gamma_max"] / (1 + 100.0 ** 2 / 2)
+    assert 0.15 < g_ratio < 0.45, g_ratio
+
+
+def test_subcycling_needs_high_order_interpolation(scan):
+    """Secs. IV-VI: with first-order interpolation sub-cycling helps little
+    (eps stays above 1 at a0 >= 50); with third order it cuts eps by an order
+    of magnitude."""
+    for a0 in (50.0, 100.0):
+        assert eps(scan, a0, 1, 0.01, 75) > 1.0
+        assert eps(scan, a0, 3, 0.01, 75) * 10 < eps(scan, a0, 3, NOSUB, 75)
+
+
+def test_standard_pic_needs_lambda_over_600_to_match(scan):
+    """Sec. VII: standard PIC reaches errors like those of order 3 + sub-
+    cycling at lambda/75 only at lambda/600 (within a factor two here), and is
+    far worse at lambda/75."""
+    for a0 in A0S:
+        new = eps(scan, a0, 3, 0.01, 75)
+        std600 = eps(scan, a0, 1, NOSUB, 600)
+        assert std600 < max(2 * new, 0.01), (a0, std600, new)
+        assert eps(scan, a0, 1, NOSUB, 75) > 5 * new, a0
+
+
+def test_chi3_peaks_near_25_at_lambda_75_and_the_peak_moves_up_with_resolution(scan):
+    """Sec. VII, Fig. 7: chi^3 = eps^1 / eps^3 (both with sub-cycling) has its
+    maximum near a0 = 25 at lambda/75; at finer resolution the maximum moves to
+    higher a0 (here past 100: chi^3 increases over the scan)."""
+    chi = {res: [eps(scan, a0, 1, 0.01, res) / eps(scan, a0, 3, 0.01, res) for a0 in A0S]
+           for res in (75, 150, 300)}
+    c75 = chi[75]
+    assert max(range(len(A0S)), key=lambda i: c75[i]) == 1, c75      # a0 = 25
+    for res in (150, 300):
+        assert all(b > a for a, b in zip(chi[res], chi[res][1:])), (res, chi[res])
+
+
+def test_fifth_order_changes_little_without_subcycling_and_helps_with_it(scan):
+    """Sec. VII: without sub-cycling, going from third to fifth order leaves
+    eps_dephasing essentially unchanged; with sub-cycling fifth order is at
+    least as good as third."""
+    for a0 in A0S:
+        e3, e5 = eps(scan, a0, 3, NOSUB, 75), eps(scan, a0, 5, NOSUB, 75)
+        assert 0.7 < e5 / e3 < 1.3, (a0, e3, e5)
+        assert eps(scan, a0, 5, 0.01, 75) <= 1.05 * eps(scan, a0, 3, 0.01, 75), a0
+
+
+def test_delta_steps_falls_with_a0_and_with_resolution(scan):
+    """Sec. VII: delta_steps = N*/(N* + N) decreases with a0 (stopping points
+    are farther apart in time) and with finer resolution (Psi scales with the
+    step), and is about the same for third and fifth order (their
+    trajectories are very similar)."""
+    for res in (75, 150, 300):
+        d = [scan[(a0, 3, 0.01, res)]["delta_steps"] for a0 in A0S]
+        assert all(b < a for a, b in zip(d, d[1:])), (res, d)
+    for a0 in A0S:
+        d75, d150, d300 = (scan[(a0, 3, 0.01, r)]["delta_steps"] for r in (75, 150, 300))
+        assert d75 > d150 > d300
+        d3, d5 = scan[(a0, 3, 0.01, 75)]["delta_steps"], scan[(a0, 5, 0.01, 75)]["delta_steps"]
+        assert abs(d5 - d3) < 0.15 * d3, (a0, d3, d5)
