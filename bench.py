@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--predict-every", type=int, default=64)
-    ap.add_argument("--heavy-budget", type=int, default=512,
+    ap.add_argument("--heavy-budget", type=int, default=1024,
                     help="sub-steps of long sub-cycles per particle and launch (0: library default, 256)")
     ap.add_argument("--batched-steps", type=int, default=200)
     ap.add_argument("--batched-ensembles", type=int, default=512)
@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-c4", action="store_true")
     ap.add_argument("--no-c5", action="store_true")
+    ap.add_argument("--study", default="reduced", choices=["none", "reduced", "full"],
+                    help="the single-electron studies of Secs. IV-VII on the GPU")
     ap.add_argument("--c5-start", type=int, default=2400,
                     help="first timed step of the self-consistent leg (the pulse inside the plasma)")
     ap.add_argument("--c4-particles", type=int, default=W.C4.n_particles)
@@ -498,6 +500,8 @@ def run_ours(args, ws, rank, local):
         net.close()
     if not args.no_c5:
         out["c5"] = run_c5(args, stream, ws)
+    if args.study != "none":
+        out["study"] = run_study(args)
     if not args.no_batched:
         out["batched"] = run_batched(args, dev, stream)
     return wl, out
@@ -614,6 +618,38 @@ def run_c5(args, stream, ws):
            "fast_forward_gauss_residual_rel": st_ff.gauss_residual / max(st_ff.rho_max, 1e-300)}
     sc.close()
     return out
+
+
+def run_study(args):
+    """The single-electron studies of Secs. IV-VII (Figs. 2, 6, 7, 8): 64
+    electrons per case over a wavelength, the Gaussian pulse sampled on the
+    grid, FP64; eps_dephasing, eps_energy and delta_steps per (a0, order,
+    sub-cycling, resolution), chi^3 = eps^1/eps^3 and chi^5 = eps^1/eps^5 with
+    sub-cycling.  reduced: a0 in {10, 25}; full: a0 in {5, 10, 25, 50, 75, 100}."""
+    from paper_2102_10983_gb300 import native
+    a0s = (10.0, 25.0) if args.study == "reduced" else (5.0, 10.0, 25.0, 50.0, 75.0, 100.0)
+    variants = [(1, 1e30, 75), (1, 0.01, 75), (3, 1e30, 75), (3, 0.01, 75), (5, 1e30, 75),
+                (5, 0.01, 75), (1, 1e30, 600), (1, 0.01, 150), (3, 0.01, 150), (5, 0.01, 150),
+                (1, 0.01, 300), (3, 0.01, 300), (5, 0.01, 300)]
+    cases = [dict(a0=a0, order=o, psi_max=ps, res=r, n_electrons=64)
+             for a0 in a0s for (o, ps, r) in variants]
+    t0 = time.perf_counter()
+    res = native.study_run(cases)
+    secs = time.perf_counter() - t0
+    table = {}
+    for c, r in zip(cases, res):
+        key = f"a0={c['a0']:g} p={c['order']} {'sub' if c['psi_max'] < 1 else 'nosub'} lambda/{c['res']}"
+        table[key] = {"eps_dephasing": r["eps_dephasing"], "eps_energy": r["eps_energy"],
+                      "delta_steps": r["delta_steps"], "N": r["N"]}
+    chi = {}
+    for a0 in a0s:
+        for res_ in (75, 150, 300):
+            e = {o: table[f"a0={a0:g} p={o} sub lambda/{res_}"]["eps_dephasing"] for o in (1, 3, 5)}
+            chi[f"a0={a0:g} lambda/{res_}"] = {"chi3": e[1] / e[3], "chi5": e[1] / e[5]}
+    return {"what": "64 electrons per case from rest, x0 over one wavelength, Gaussian pulse "
+                    "(sigma = 8 pi) sampled on the grid, c dt/dx = 0.99, Psi_max = 0.01 with "
+                    "sub-cycling; maxima over the electrons", "seconds": secs,
+            "cases": len(cases), "table": table, "chi": chi}
 
 
 def run_learned(args, make, start, Wu, K, last, n_e, ws, stream):
@@ -808,6 +844,8 @@ def main():
         line["c4"] = out["c4"]
     if "c5" in out:
         line["c5"] = out["c5"]
+    if "study" in out:
+        line["study"] = out["study"]
     if "batched" in out:
         b = out["batched"]
         ach = bytes_per * b["electrons"] / (b["ms_per_step"] / 1e3) / 1e9

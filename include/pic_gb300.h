@@ -321,6 +321,43 @@ int pic_batch_autotune(pic_batch* b, int64_t n, int32_t steps, int32_t* chunk_ou
 
 const char* pic_batch_last_error(const pic_batch* b);
 
+/* ---- single-electron studies of Secs. IV-VII ------------------------------
+ * Electrons from rest through the Gaussian-enveloped plane wave of Eqs.
+ * laser5 - laser3, a = a0 exp(-(xi - xi0)^2 / (2 sigma^2)) sin xi,
+ * E_y = B_z = -da/dxi, sampled on the grid (E_y at i dx, n dt; B_z at
+ * (i + 1/2) dx, (n + 1/2) dt: the "perfectly propagating PIC" of Sec. III) and
+ * pushed with the method (FP64, Algorithm 1, order-p Lagrange in time, tent
+ * in space).  Each case runs n_electrons electrons with x0 = j lambda /
+ * n_electrons (j = 0 .. n_electrons - 1) for n_steps macro steps. */
+typedef struct {
+  double a0, xi0, sigma;  /* pulse (normalized units, lambda = 2 pi)                */
+  double dt, dx;          /* macro step and cell                                    */
+  double psi_max;         /* criterion threshold; a huge value turns sub-cycling off */
+  double qm;              /* charge / mass, -1                                       */
+  int32_t order, k_max, field_time;
+  int32_t n_electrons;    /* 1 .. 256                                                */
+  int64_t n_steps;
+} pic_study_case;
+
+typedef struct {
+  /* maxima over the case's electrons and macro steps: eps_dephasing =
+   * |R - 1| with R = gamma - p_x (Sec. IV, Eq. R error); eps_energy =
+   * |gamma - gamma_th| / gamma_th with gamma_th = 1 + a^2/2 at the momentum's
+   * phase (Eq. gamma error); gamma_max */
+  double eps_dephasing, eps_energy, gamma_max;
+  double eps_dephasing_first, eps_energy_first, gamma_max_first;  /* electron j = 0 */
+  double n_star_mean;     /* N* (sub-steps of macro steps with k > 0, Sec. VII), mean */
+  int64_t n_steps;        /* N */
+  int64_t n_star_first;   /* N* of electron j = 0                                   */
+  int64_t substeps;       /* Boris sub-steps, all electrons                          */
+  int64_t k_hist[8];      /* macro steps per k, all electrons                        */
+} pic_study_result;
+
+/* Run n_cases (1 .. 65535) study cases on the GPU (host arrays; allocates
+ * temporary device memory; synchronizes the stream).  Errors: PIC_EINVAL,
+ * PIC_ENOMEM, PIC_ECUDA. */
+int pic_study_run(const pic_study_case* cases, int32_t n_cases, pic_study_result* out, void* stream);
+
 /* Allocation-free variant of the binned mixed-precision push (no counterpart
  * in the paper: it exists for host programs that may not call cudaMalloc at
  * push time, e.g. because another framework owns and carves up all device

@@ -18,8 +18,7 @@ from concurrent.futures import ThreadPoolExecutor
 
 from . import lib as _orc_lib
 
-SIGMA = 8 * math.pi
-XI0 = 6 * SIGMA
+from paper_2102_10983_gb300.workloads import STUDY_SIGMA as SIGMA, STUDY_XI0 as XI0, study_steps
 
 
 class TrjParams(ctypes.Structure):
@@ -54,11 +53,7 @@ def _lib():
 
 
 def n_steps_for(a0: float, dt: float) -> int:
-    from scipy.integrate import quad
-    xi_end = 2 * XI0
-    f = lambda s: 0.5 * (a0 * math.exp(-((s - XI0) ** 2) / (2 * SIGMA ** 2)) * math.sin(s)) ** 2
-    t_end = xi_end + quad(f, 0, xi_end, limit=4000)[0]
-    return int(t_end / dt) + 1
+    return study_steps(a0, dt)
 
 
 def params(a0: float, order: int, psi_max: float, res: float, k_max: int = 7,

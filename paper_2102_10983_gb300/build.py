@@ -31,6 +31,7 @@ SOURCES = {
     "mlp_api.cu": [],
     "mlp_tc.cu": [],
     "pic_sc1d.cu": ["-fmad=false"],
+    "study.cu": ["-fmad=false"],
 }
 
 

@@ -9,6 +9,7 @@ library is missing or fails to load, ``lib()`` raises.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 
 import numpy as np
@@ -71,6 +72,33 @@ class PicSc1dStats(ctypes.Structure):
                 "checks": self.checks}
 
 
+class PicStudyCase(ctypes.Structure):
+    _fields_ = [("a0", ctypes.c_double), ("xi0", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("dt", ctypes.c_double), ("dx", ctypes.c_double), ("psi_max", ctypes.c_double),
+                ("qm", ctypes.c_double), ("order", ctypes.c_int32), ("k_max", ctypes.c_int32),
+                ("field_time", ctypes.c_int32), ("n_electrons", ctypes.c_int32),
+                ("n_steps", ctypes.c_int64)]
+
+
+class PicStudyResult(ctypes.Structure):
+    _fields_ = [("eps_dephasing", ctypes.c_double), ("eps_energy", ctypes.c_double),
+                ("gamma_max", ctypes.c_double), ("eps_dephasing_first", ctypes.c_double),
+                ("eps_energy_first", ctypes.c_double), ("gamma_max_first", ctypes.c_double),
+                ("n_star_mean", ctypes.c_double), ("n_steps", ctypes.c_int64),
+                ("n_star_first", ctypes.c_int64), ("substeps", ctypes.c_int64),
+                ("k_hist", ctypes.c_int64 * 8)]
+
+    def as_dict(self) -> dict:
+        n, ns = self.n_steps, self.n_star_mean
+        return {"eps_dephasing": self.eps_dephasing, "eps_energy": self.eps_energy,
+                "gamma_max": self.gamma_max, "eps_dephasing_first": self.eps_dephasing_first,
+                "eps_energy_first": self.eps_energy_first,
+                "gamma_max_first": self.gamma_max_first, "N": n, "N_star_mean": ns,
+                "N_star_first": self.n_star_first,
+                "delta_steps": ns / (ns + n) if n + ns else 0.0, "substeps": self.substeps,
+                "k_hist": list(self.k_hist)}
+
+
 # (name, restype, argtypes) of every symbol declared in include/*.h
 _VP, _I32, _I64, _D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
 SIGNATURES = {
@@ -115,6 +143,8 @@ SIGNATURES = {
     "pic_push_mixed_noalloc": (ctypes.c_int, [ctypes.POINTER(PicParams), _I64, _VP, _VP, _VP, _VP,
                                               _VP, _VP, _VP, _VP, _VP, _I64, _I64, _I64, _VP,
                                               ctypes.POINTER(PicStepStats)]),
+    "pic_study_run": (ctypes.c_int, [ctypes.POINTER(PicStudyCase), _I32,
+                                     ctypes.POINTER(PicStudyResult), _VP]),
     "pic_sc1d_create": (ctypes.c_int, [ctypes.POINTER(PicSc1dParams), _I64, _VP,
                                        ctypes.POINTER(_VP)]),
     "pic_sc1d_destroy": (ctypes.c_int, [_VP]),
@@ -525,3 +555,24 @@ class Sc1d:
         out = [np.empty(self.M) for _ in range(3)]
         self.fields_read(level, *out)
         return out
+
+
+def study_run(cases, stream=None):
+    """pic_study_run on a list of dicts (a0, order, psi_max, res, n_electrons
+    and optionally k_max, field_time, n_steps): lambda/(c dt) = res,
+    c dt/dx = 0.99, the pulse of workloads.STUDY_*; returns result dicts."""
+    from . import workloads as Wl
+    arr = (PicStudyCase * len(cases))()
+    for q, c in zip(arr, cases):
+        dt = 2 * math.pi / c["res"]
+        n_e = int(c.get("n_electrons", 1))
+        steps = c.get("n_steps") or Wl.study_steps(c["a0"], dt, x_span=2 * math.pi * (n_e - 1) / n_e)
+        q.a0, q.xi0, q.sigma = float(c["a0"]), Wl.STUDY_XI0, Wl.STUDY_SIGMA
+        q.dt, q.dx, q.psi_max, q.qm = dt, dt / 0.99, float(c["psi_max"]), -1.0
+        q.order, q.k_max, q.field_time = int(c["order"]), int(c.get("k_max", 7)), int(c.get("field_time", 0))
+        q.n_electrons, q.n_steps = n_e, int(steps)
+    out = (PicStudyResult * len(cases))()
+    code = lib().pic_study_run(arr, len(cases), out, _stream_handle(stream))
+    if code != PIC_OK:
+        raise PicError(code, (lib().pic_last_error(None) or b"").decode())
+    return [r.as_dict() for r in out]

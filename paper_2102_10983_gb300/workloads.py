@@ -313,3 +313,24 @@ def laser_plasma_c5(n_cells: int = 20_000, ppc: int = 100, a0: float = 150.0) ->
     return LaserPlasma1D(name=f"c5_laser_plasma_a0_{a0:g}_{n_cells}cells_{ppc}ppc", n_cells=n_cells,
                          a0=a0, fwhm=fwhm, x_front=x_front, x_top=x_top, scale_length=L,
                          n_top=0.5, ppc=ppc)
+
+
+# ---------------------------------------------------------------- single-electron studies
+
+# The Gaussian-enveloped pulse of the studies of Secs. IV-VII (Eq. laser1,
+# sigma = 8 pi), centred 6 sigma ahead of an electron at x = 0 (where the field
+# is below a0 e^-18).
+STUDY_SIGMA = 8 * math.pi
+STUDY_XI0 = 6 * STUDY_SIGMA
+
+
+def study_steps(a0: float, dt: float, x_span: float = 0.0) -> int:
+    """Macro steps until an electron from rest at x0 <= x_span is through the
+    pulse: t = x0 + 2 xi0 + int_0^{2 xi0} a^2/2 dxi (t - x = xi, dx/dxi = a^2/2
+    for R = 1)."""
+    from scipy.integrate import quad
+    xi_end = 2 * STUDY_XI0
+    f = lambda s: 0.5 * (a0 * math.exp(-((s - STUDY_XI0) ** 2) / (2 * STUDY_SIGMA ** 2))
+                         * math.sin(s)) ** 2
+    t_end = x_span + xi_end + quad(f, 0, xi_end, limit=4000)[0]
+    return int(t_end / dt) + 1
