@@ -57,7 +57,9 @@ def parse():
     ap.add_argument("--predict-every", type=int, default=64)
     ap.add_argument("--heavy-budget", type=int, default=1024,
                     help="sub-steps of long sub-cycles per particle and launch (0: library default, 256)")
-    ap.add_argument("--batched-steps", type=int, default=200)
+    ap.add_argument("--batched-steps", type=int, default=5000)
+    ap.add_argument("--batched-chunk", type=int, default=500,
+                    help="steps per graph-captured call of the batched leg")
     ap.add_argument("--batched-ensembles", type=int, default=512)
     ap.add_argument("--cpu-sample", type=int, default=16384)
     ap.add_argument("--no-plain", action="store_true")
@@ -238,57 +240,95 @@ def batched_workload(n_ens: int, seed: int = 3):
     return ens
 
 
-def run_batched(args, dev, stream):
-    """The batched ensembles: autotuned, graph-captured multi-step launch."""
+# FP32 work of a Boris sub-step of the mixed form's sub-cycle, counted from
+# its source in FP32-pipe instructions (an FMA is one): Horner's rule at the
+# four tent nodes 12, tent weights and the two interpolations 7, the sub-step
+# time 1, the Boris rotation and the position update 24 (plus 3 SFU
+# reciprocal square roots / reciprocals, not counted).  Measured FP32 issue
+# peak: 117 FFMA per clock per SM.
+F32_OPS_PER_SUBSTEP = 44
+FFMA_PER_CLK_PER_SM = 117
+
+
+def run_batched(args, dev, stream, sms):
+    """The batched ensembles: autotuned, graph-captured multi-step launches
+    over all the workload's steps, in calls of --batched-chunk steps whose
+    field levels are uploaded between calls (outside the timed region)."""
     import torch
     from paper_2102_10983_gb300 import native
     ens = batched_workload(args.batched_ensembles)
     p, K, Wn = 3, args.batched_steps, 512
+    C = max(1, min(args.batched_chunk, K))
     b = native.Batch([dict(dt=wl.dt, dx=wl.dx, psi_max=wl.psi_max, n_particles=wl.n_particles)
-                      for wl in ens], order=p, window=Wn, ring_levels=K + p + 8, stream=stream)
+                      for wl in ens], order=p, window=Wn, ring_levels=C + p + 8, stream=stream)
     inis = [wl.particles() for wl in ens]
     b.particles_write(*[np.concatenate([getattr(i, f) for i in inis]) for f in ("x", "px", "py", "pz")])
     del inis
     n_total = b.n_total
-    # levels -p .. K+3 of every ensemble, generated on the device
     dts = torch.tensor([wl.dt for wl in ens], dtype=torch.float64, device=dev)[:, None]
     dxs = torch.tensor([wl.dx for wl in ens], dtype=torch.float64, device=dev)[:, None]
     a0s = torch.tensor([wl.a0 for wl in ens], dtype=torch.float64, device=dev)[:, None]
     c = torch.arange(Wn, dtype=torch.float64, device=dev)[None, :]
-    origins = np.stack([wl.origins(-p, K + p + 4) for wl in ens])  # (n_ens, levels)
+    origins = np.stack([wl.origins(-p, K + p + 4) for wl in ens])  # (n_ens, levels -p .. K+3)
 
-    def level(r):
-        n = float(r - p)
+    def upload(level):
+        r = level + p
+        n = float(level)
         i0 = torch.as_tensor(origins[:, r], dtype=torch.float64, device=dev)[:, None]
         xiE = n * dts - (i0 + c) * dxs
         xiB = (n + 0.5) * dts - (i0 + c + 0.5) * dxs
         E = torch.where(xiE > 0, -a0s * torch.cos(xiE), torch.zeros_like(xiE)).contiguous()
         B = torch.where(xiB > 0, -a0s * torch.cos(xiB), torch.zeros_like(xiB)).contiguous()
-        return origins[:, r], E, B
+        b.fields_upload(level, origins[:, r], E, B)
 
-    for r in range(K + p + 4):
-        i0, E, B = level(r)
-        b.fields_upload(r - p, i0, E, B)
+    top = -p - 1  # highest level in the ring
+    def fill(last):
+        nonlocal top
+        for lv in range(top + 1, last + 1):
+            upload(lv)
+        top = max(top, last)
+
+    fill(min(C, K) + 3)
     chunk, blocks, tune_ms = b.autotune(0, 4)
     b.config(chunk=chunk, blocks_per_sm=blocks, use_graph=True)
     torch.cuda.synchronize()
     launches0 = b.launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    st = b.push_step(0, K)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    ms = 0.0
+    k_hist = [0] * 8
+    substeps = out_of_window = 0
+    for s0 in range(0, K, C):
+        n = min(C, K - s0)
+        fill(s0 + n + 3)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        st = b.push_step(s0, n)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        k_hist = [u + v for u, v in zip(k_hist, st.k_hist)]
+        substeps += st.substeps
+        out_of_window += st.out_of_window
+    clk = clocks.stop()
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    ops = substeps * F32_OPS_PER_SUBSTEP / (ms / 1e3)
+    peak = sms * FFMA_PER_CLK_PER_SM * sm_mhz * 1e6
     out = {"workload": f"{len(ens)} ensembles, a0 x lambda/(c dt) x Psi_max cycled over "
                        "{10,30,100,300} x {25,50,75,150} x {0.003,0.01,0.03}, sizes log-uniform "
-                       "[1e3, 1e6], electrons at rest, steps 0..%d" % (K - 1),
+                       "[1e3, 1e6], electrons at rest, steps 0..%d in calls of %d" % (K - 1, C),
            "electrons": int(n_total), "steps": K,
            "value": n_total * K / (ms / 1e3), "unit": UNIT,
-           "substeps_per_s": st.substeps / (ms / 1e3),
+           "substeps_per_s": substeps / (ms / 1e3), "substeps_per_particle_step": substeps / (n_total * K),
            "ms_per_step": ms / K, "autotuned": {"chunk": chunk, "blocks_per_sm": blocks,
                                                  "trial_ms_per_step": tune_ms},
            "graph_captured": True, "gpu_launches": b.launches() - launches0,
-           "k_hist": list(st.k_hist), "out_of_window": st.out_of_window}
+           "k_hist": k_hist, "out_of_window": out_of_window, "clocks": clk,
+           "roofline": {"bound": "alu", "achieved": ops, "peak": peak, "unit": "FP32 ops/s",
+                        "frac": ops / peak,
+                        "model": f"{F32_OPS_PER_SUBSTEP} FP32 instructions per Boris sub-step; peak "
+                                 f"= SMs x {FFMA_PER_CLK_PER_SM} FFMA/clk x SM clock"}}
     b.close()
     return out
 
@@ -375,11 +415,11 @@ def run_ours(args, ws, rank, local):
     E, B, i0 = device_levels(wl, -p, last + p, dev)
     ring = last + p + 1
 
-    def make(precision, schedule, levels_upto, state=None, w=wl, Ed=E, Bd=B, io=i0):
+    def make(precision, schedule, levels_upto, state=None, w=wl, Ed=E, Bd=B, io=i0, carry=0):
         integ = native.Integrator(w.dt, w.dx, w.psi_max, order=p, precision=precision,
                                   schedule=schedule, capacity=w.n_particles, window=w.window,
                                   ring_levels=levels_upto + p + 1, stream=stream,
-                                  heavy_budget=args.heavy_budget)
+                                  heavy_budget=args.heavy_budget, carry=carry)
         if state is None:
             integ.pic_particles_write(ini.x, ini.px, ini.py, ini.pz)
         else:
@@ -471,8 +511,13 @@ def run_ours(args, ws, rank, local):
 
     # ---- end to end through the C ABI with host buffers
     if not args.no_e2e:
+        # the headline's schedule, one step per call (as a PIC code's loop calls
+        # it after each field update), long sub-cycles carried between calls
         Ke = min(K, args.e2e_steps)
-        integ = make(native.PIC_MIXED, sched, start + Wu)
+        e_sched = native.PIC_SCHED_PREDICTED if net is not None else sched
+        integ = make(native.PIC_MIXED, e_sched, start + Wu, carry=1)
+        if net is not None:
+            integ.attach_predictor(net, args.predict_every)
         integ.pic_push_step(0, start + Wu, want_stats=False)
         hostE = torch.empty((Ke, wl.window), dtype=torch.float64).pin_memory()
         hostB = torch.empty((Ke, wl.window), dtype=torch.float64).pin_memory()
@@ -486,11 +531,17 @@ def run_ours(args, ws, rank, local):
             integ.pic_fields_upload(s, int(i0[s + p]), hostE[r], hostB[r])
             integ.pic_push_step(s, 1, want_stats=True,
                                 ok=(native.PIC_OK, native.PIC_ERANGE, native.PIC_EKMAX))
+        integ.pic_finish()  # the last step's carried sub-cycles
+        torch.cuda.synchronize()
         t1 = time.perf_counter()
         barrier(ws)
         integ.close()
         e2e_s = max_over_ranks(ws, t1 - t0)
         out["e2e"] = {"value": n_e * Ke * ws / e2e_s, "unit": UNIT, "steps": Ke,
+                      "schedule": "predicted (learned)" if net is not None else args.schedule,
+                      "call": "per step: pic_fields_upload of the level from pinned host memory, "
+                              "pic_push_step with stats (synchronizing read-back), carry = 1; "
+                              "pic_finish at the end",
                       "h2d_bytes_per_step": 2 * wl.window * 8,
                       "d2h_bytes_per_step": int(native.ctypes.sizeof(native.PicStepStats))}
     del E, B
@@ -503,7 +554,7 @@ def run_ours(args, ws, rank, local):
     if args.study != "none":
         out["study"] = run_study(args)
     if not args.no_batched:
-        out["batched"] = run_batched(args, dev, stream)
+        out["batched"] = run_batched(args, dev, stream, sms)
     return wl, out
 
 
@@ -849,9 +900,7 @@ def main():
     if "batched" in out:
         b = out["batched"]
         ach = bytes_per * b["electrons"] / (b["ms_per_step"] / 1e3) / 1e9
-        b["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                         "frac": ach / hbm, "note": "42 B per electron-step over the whole step "
-                                                   "(push and per-step field kernels)"}
+        b["hbm_frac"] = ach / hbm  # 42 B per electron-step: not what bounds this leg
         line["batched"] = b
     if not args.no_cpu_baseline:
         threads = args.cpu_threads or os.cpu_count() or 1

@@ -92,12 +92,26 @@ typedef struct {
                            sub-cycle may take per launch; the rest continues in
                            the next launch while the particle runs behind the
                            stream and then catches up (the same bits either
-                           way; a call finishes every particle).  0: 256;
-                           < 0: no limit                                      */
+                           way; a call finishes every particle unless carry
+                           is set).  0: 256; < 0: no limit                    */
   int32_t diagnostics; /* PIC_FP64 form: PIC_DIAG_WORK accumulates, per particle,
                           the work of the electric field over every Boris push
                           (App. B; read with pic_work_read); 0: none          */
-  int32_t reserved;
+  int32_t carry;      /* binned schedules, for programs that push one step (or
+                         a few) per call, each after uploading the next field
+                         level.  0: every call ends with a closing launch that
+                         finishes the long sub-cycles its last step deferred.
+                         c >= 1: they are carried into the next call instead,
+                         where they run beside the next step's stream; a
+                         particle may then be left up to c - 1 steps behind a
+                         call's last step (ring_levels >= order + 1 + c).
+                         While sub-cycles are carried the particle store is
+                         mid-step: pic_particles_read, pic_features,
+                         pic_predict and pic_attach_predictor first finish them
+                         (as pic_finish), as does a pic_push_step whose first
+                         step does not follow the last one pushed, and
+                         pic_fields_upload refuses to replace a level they
+                         still need.  Same bits as carry = 0.                 */
 } pic_params;
 
 /* pic_params.diagnostics */
@@ -146,6 +160,9 @@ int pic_particles_read(pic_ctx* ctx, double* x, double* px, double* py, double* 
  * context's window), each W FP64 values in `where` memory.  The level replaces
  * the oldest one in the ring (slot level mod ring_levels).  (Eqs. eq:Ey,
  * eq:Bz give the staggering; Sec. VI the history the interpolation needs.)
+ * With pic_params.carry = c the slot must not hold a level that carried
+ * sub-cycles still need (PIC_EINVAL, nothing written): after a call whose
+ * last step was `last`, levels last - c + 1 - order .. last.
  * Errors: PIC_EINVAL, PIC_ECUDA. */
 int pic_fields_upload(pic_ctx* ctx, int64_t level, int64_t i0, const double* Ey,
                       const double* Bz, int32_t where);
@@ -169,6 +186,13 @@ int pic_push_step(pic_ctx* ctx, int64_t n, int64_t n_steps, pic_step_stats* stat
  * and after it; compare with the kinetic energy gamma - 1.  work: n FP64 in
  * `where` memory.  Errors: PIC_EINVAL (not enabled), PIC_ECUDA. */
 int pic_work_read(pic_ctx* ctx, double* work, int64_t n, int32_t where);
+
+/* With pic_params.carry: finish every long sub-cycle carried from the last
+ * call (one closing launch, queued on the stream) and return the status bytes
+ * to their public form.  Needs the levels of the carried steps, which
+ * pic_fields_upload keeps.  No-op when nothing is carried (any schedule or
+ * form).  Errors: PIC_EINVAL, PIC_ECUDA. */
+int pic_finish(pic_ctx* ctx);
 
 /* Read (and optionally reset) the accumulated counters.  Synchronizes. */
 int pic_stats_read(pic_ctx* ctx, pic_step_stats* stats, int32_t reset);
@@ -367,8 +391,9 @@ int pic_study_run(const pic_study_case* cases, int32_t n_cases, pic_study_result
  * every GPU loading the library holds until the process exits.  Nothing is
  * allocated: no cudaMalloc/cudaFree, no allocating library call.
  *
- *  prm:        as for pic_create; precision must be PIC_MIXED and schedule
- *              PIC_SCHED_BINNED.
+ *  prm:        as for pic_create; precision must be PIC_MIXED, schedule
+ *              PIC_SCHED_BINNED, diagnostics and carry 0 (every call
+ *              finishes its particles).
  *  n_particles <= 65,536 (the size the static queues hold); larger counts are
  *              rejected with PIC_EINVAL.
  *  cell, frac, px, py, pz, status: device arrays of n_particles entries in the

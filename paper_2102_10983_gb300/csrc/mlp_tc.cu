@@ -313,13 +313,20 @@ __global__ void __launch_bounds__(kTcThreads) predict_tc_kernel(PushArgsMixed a,
   tc_begin(s, Pm);
   uint32_t ph = 0;
   const int64_t n_groups = (a.n + kTcThreads - 1) / kTcThreads;
-  for (int64_t t = blockIdx.x; t < n_groups; t += gridDim.x) {
+  // each tile's particle loads are issued before the previous tile's network
+  // runs, so their DRAM latency overlaps the MMA round trips
+  int64_t t = blockIdx.x;
+  FeatureInput cur = feature_input(a, t * kTcThreads + threadIdx.x);
+  for (; t < n_groups; t += gridDim.x) {
     const int64_t i = t * kTcThreads + threadIdx.x;
+    const int64_t tn = t + gridDim.x;
+    const FeatureInput nxt = feature_input(a, tn < n_groups ? tn * kTcThreads + threadIdx.x : a.n);
     float f[6];
-    particle_features(a, a.halfE, a.halfB, a.lo, a.hi, i, f);
+    features_of(a, a.halfE, a.halfB, a.lo, a.hi, cur, f);
     const int c = tc_tiles(s, f, ph);
     if (i < a.n) pred[i] = (uint8_t)c;
     if (s.failed) break;
+    cur = nxt;
   }
   if (s.failed && threadIdx.x == 0 && a.stats) atomicExch(&a.stats->error, 2);
   tc_end(s);

@@ -53,6 +53,12 @@ struct pic_ctx {
   int32_t* pred_queue = nullptr;
   const pic_mlp* mlp = nullptr;
   int32_t predict_every = 1;
+  // pic_params.carry: long sub-cycles left by the last call for the next one
+  bool open = false;       // some may be carried (the particle store is mid-step)
+  int64_t open_last = 0;   // the last step pushed
+  int64_t open_step0 = 0;  // base of lag_step for the run of carried calls
+  int64_t open_keep = 0;   // the oldest step a carried particle may be in
+  int64_t run_j = 0;       // binned launches of the run: parities, queue buffers, refresh cadence
 
   int64_t launches = 0;
   // optional CUDA-event timing of push steps
@@ -82,6 +88,8 @@ static int fail(pic_ctx* c, int code, const char* fmt, const char* detail = "") 
   } while (0)
 
 static bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+static int close_open(pic_ctx* c);
 
 static void free_events(pic_ctx* c) {
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -199,6 +207,10 @@ extern "C" int pic_create(const pic_params* prm, int64_t capacity, int64_t windo
     return fail(nullptr, PIC_EINVAL, "pic_create: the binned schedules need PIC_MIXED%s");
   if (prm->diagnostics != 0 && (prm->diagnostics != PIC_DIAG_WORK || prm->precision != PIC_FP64))
     return fail(nullptr, PIC_EINVAL, "pic_create: PIC_DIAG_WORK is the only diagnostic (FP64 form)%s");
+  if (prm->carry < 0 || prm->carry > (1 << 16) || (prm->carry > 0 && prm->schedule == PIC_SCHED_PLAIN))
+    return fail(nullptr, PIC_EINVAL, "pic_create: carry must be 0, or 1..65536 with a binned schedule%s");
+  if (prm->carry > 0 && (int64_t)ring_levels < (int64_t)prm->order + 1 + prm->carry)
+    return fail(nullptr, PIC_EINVAL, "pic_create: carry = c needs ring_levels >= order + 1 + c%s");
   if (capacity < 0 || capacity > ((int64_t)1 << 31) - 1)
     return fail(nullptr, PIC_EINVAL, "pic_create: capacity must be 0..2^31-1%s");
   if (!is_pow2(window_cells) || window_cells < 16 || window_cells > ((int64_t)1 << 30))
@@ -367,6 +379,11 @@ extern "C" int pic_particles_write(pic_ctx* c, const double* x, const double* px
   if (n < 0 || n > c->capacity) return fail(c, PIC_EINVAL, "pic_particles_write: n out of range%s");
   if (where != PIC_HOST && where != PIC_DEVICE) return fail(c, PIC_EINVAL, "bad where%s");
   if (n > 0 && (!x || !px || !py || !pz)) return fail(c, PIC_EINVAL, "pic_particles_write: NULL array%s");
+  if (c->open) {  // new particles replace any carried sub-cycles: drop their queues
+    c->open = false;
+    c->run_j = 0;
+    CUDA_TRY(c, cudaMemsetAsync(c->qcount, 0, 64 * 4, c->stream));
+  }
   c->n = n;
   if (n == 0) return PIC_OK;
   if (status)
@@ -412,6 +429,8 @@ extern "C" int pic_particles_read(pic_ctx* c, double* x, double* px, double* py,
   if (!c) return PIC_EINVAL;
   if (n < 0 || n > c->n) return fail(c, PIC_EINVAL, "pic_particles_read: n exceeds the loaded count%s");
   if (where != PIC_HOST && where != PIC_DEVICE) return fail(c, PIC_EINVAL, "bad where%s");
+  int rc = close_open(c);  // carried sub-cycles first: the store is then whole
+  if (rc != PIC_OK) return rc;
   if (n == 0) return PIC_OK;
   if (status)
     CUDA_TRY(c, cudaMemcpyAsync(status, c->status, (size_t)n, kind_out(where), c->stream));
@@ -456,6 +475,13 @@ extern "C" int pic_fields_upload(pic_ctx* c, int64_t level, int64_t i0, const do
     return fail(c, PIC_EINVAL, "pic_fields_upload: window origin out of range%s");
   const int64_t W = c->W;
   const int32_t slot = (int32_t)(((level % c->R) + c->R) % c->R);
+  if (c->open) {
+    const int64_t old = c->slot_level[slot];
+    if (old != INT64_MIN && old >= c->open_keep - c->prm.order && old <= c->open_last)
+      return fail(c, PIC_EINVAL,
+                  "pic_fields_upload: the slot holds a level that carried sub-cycles still need "
+                  "(push the next step or call pic_finish first)%s");
+  }
   const double* e = Ey;
   const double* b = Bz;
   if (where == PIC_HOST) {
@@ -580,6 +606,99 @@ static void fill_mixed(pic_ctx* c, PushArgsMixed& a, int64_t s, int64_t lo, int6
   }
 }
 
+// Launch arguments of the mixed form common to every launch of a call.
+static void mixed_base(pic_ctx* c, PushArgsMixed& base) {
+  memset(&base, 0, sizeof(base));
+  base.n = c->n;
+  base.cell = c->cell; base.frac = c->frac; base.px = c->fpx; base.py = c->fpy; base.pz = c->fpz;
+  base.status = c->status;
+  base.tma = (((uintptr_t)c->cell | (uintptr_t)c->frac | (uintptr_t)c->fpx | (uintptr_t)c->fpy |
+               (uintptr_t)c->fpz | (uintptr_t)c->status) & 15) == 0;
+  base.mask = (int32_t)(c->W - 1);
+  base.dt = (float)c->prm.dt;
+  base.psi_max = (float)c->prm.psi_max;
+  base.qm = (float)c->prm.qm;
+  base.qm_abs = fabsf((float)c->prm.qm);
+  base.inv_dx = (float)(1.0 / c->prm.dx);
+  base.k_max = c->prm.k_max;
+  base.field_time = c->prm.field_time;
+  lagrange_monomials(c->prm.order, base.mono);
+  base.wtab = c->wtab32;
+  base.crit_row = wrows_total(c->prm.k_max) - 1;
+  base.stats = c->dstats;
+  base.qcap = c->capacity;
+  base.keep_step = INT64_MIN;
+  if (c->prm.schedule != PIC_SCHED_PLAIN) {
+    base.cursor = (int*)(c->qcount + 16);
+    base.blocks_done = (unsigned*)(c->qcount + 18);
+    // deferred particles may run behind the stream: the kernel finds any
+    // step's levels in the ring from the slots' origins
+    base.lag_step = c->lag_step;
+    base.lag_j = c->lag_j;
+    base.heavy_budget = c->heavy_budget;
+    base.ring_R = c->R;
+    base.slot_i0 = c->dslot_i0;  // kept current by pic_fields_upload, in stream order
+  }
+}
+
+// The closing launch after step s (a: that step's launch arguments, J its
+// index in the run, coef_s its node table): every deferred particle is brought
+// to the end of step s and the status bytes return to the public form.
+static cudaError_t closing_launch(pic_ctx* c, const PushArgsMixed& a, int64_t s, int64_t lo,
+                                  int64_t hi, int64_t J, const float* coef_s, int* launches) {
+  const int64_t qsz = 7 * c->capacity;
+  PushArgsMixed f = a;
+  fill_mixed(c, f, s, lo, hi, true);
+  f.queue_in = c->queue + ((J + 1) & 1) * qsz;
+  f.qcount_in = c->qcount + ((J + 1) & 1) * 8;
+  f.queue_out = c->queue + (J & 1) * qsz;
+  f.qcount_out = c->qcount + (J & 1) * 8;
+  f.finalize = 1;
+  f.step_cur = s + 1;
+  f.coef_p = coef_s;  // the deferred work finishes step s
+  f.keep_step = INT64_MIN;
+  f.pred_queue = nullptr;
+  f.pred_count = nullptr;
+  return launch_binned_step(f, c->prm.order, c->sm_count, c->stream, launches);
+}
+
+// Finish what carried calls left (pic_params.carry): the closing launch of the
+// last step pushed.
+static int close_open(pic_ctx* c) {
+  if (!c->open) return PIC_OK;
+  const int64_t S = c->open_last;
+  int slots[kMaxOrder + 1];
+  int64_t lo, hi;
+  // the levels of the carried steps are kept by pic_fields_upload
+  int rc = step_slots(c, S, slots, &lo, &hi);
+  if (rc != PIC_OK) return rc;
+  PushArgsMixed a;
+  mixed_base(c, a);
+  a.step0 = c->open_step0;
+  a.step_cur = S;
+  fill_mixed(c, a, S, lo, hi, false);
+  const int64_t coef_stride = c->W * 2 * (c->prm.order + 1);
+  const float* coef_s = c->coef + (S & 1) * coef_stride;
+  a.coef = coef_s;
+  a.halfE = c->half;
+  a.halfB = c->half + c->W + 1;
+  const int64_t J = c->run_j - 1;
+  a.parity_cur = (int)(J & 1);
+  a.parity_next = (int)((J + 1) & 1);
+  int launches = 0;
+  cudaError_t e = closing_launch(c, a, S, lo, hi, J, coef_s, &launches);
+  c->launches += launches;
+  c->open = false;
+  c->run_j = 0;
+  if (e != cudaSuccess) return fail(c, PIC_ECUDA, "closing launch: %s", cudaGetErrorString(e));
+  return PIC_OK;
+}
+
+extern "C" int pic_finish(pic_ctx* c) {
+  if (!c) return PIC_EINVAL;
+  return close_open(c);
+}
+
 extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_stats* stats) {
   if (!c) return PIC_EINVAL;
   if (n_steps < 1) return fail(c, PIC_EINVAL, "pic_push_step: n_steps must be >= 1%s");
@@ -587,6 +706,7 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
   const int64_t W = c->W;
   const bool binned = c->prm.schedule != PIC_SCHED_PLAIN;
   const bool predicted = c->prm.schedule == PIC_SCHED_PREDICTED && c->mlp != nullptr;
+  const bool carry = binned && c->prm.carry > 0;
   // validate every step's levels before queuing anything
   for (int64_t s = n; s < n + n_steps; ++s) {
     int slots[kMaxOrder + 1];
@@ -596,42 +716,24 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
     if (c->prm.precision == PIC_MIXED && (lo < -((int64_t)1 << 30) || hi > ((int64_t)1 << 30)))
       return fail(c, PIC_EINVAL, "pic_push_step: mixed form needs node indices within +-2^30%s");
   }
+  // carried work continues only into the step after the last one pushed (and
+  // while lag_step, relative to the run's first step, fits its 32 bits)
+  if (c->open && (n != c->open_last + 1 || n + n_steps - c->open_step0 > ((int64_t)1 << 30))) {
+    int rc = close_open(c);
+    if (rc != PIC_OK) return rc;
+  }
+  const bool cont = c->open;  // this call's first launch takes over carried work
+  const int64_t J0 = cont ? c->run_j : 0;
   PushArgsMixed base;
-  memset(&base, 0, sizeof(base));
   if (c->prm.precision == PIC_MIXED) {
-    base.n = c->n;
-    base.cell = c->cell; base.frac = c->frac; base.px = c->fpx; base.py = c->fpy; base.pz = c->fpz;
-    base.status = c->status;
-    base.tma = (((uintptr_t)c->cell | (uintptr_t)c->frac | (uintptr_t)c->fpx | (uintptr_t)c->fpy |
-                 (uintptr_t)c->fpz | (uintptr_t)c->status) & 15) == 0;
-    base.mask = (int32_t)(W - 1);
-    base.dt = (float)c->prm.dt;
-    base.psi_max = (float)c->prm.psi_max;
-    base.qm = (float)c->prm.qm;
-    base.qm_abs = fabsf((float)c->prm.qm);
-    base.inv_dx = (float)(1.0 / c->prm.dx);
-    base.k_max = c->prm.k_max;
-    base.field_time = c->prm.field_time;
-    lagrange_monomials(c->prm.order, base.mono);
-    base.wtab = c->wtab32;
-    base.crit_row = wrows_total(c->prm.k_max) - 1;
-    base.stats = c->dstats;
-    base.qcap = c->capacity;
-    if (binned) {
-      base.cursor = (int*)(c->qcount + 16);
-      base.blocks_done = (unsigned*)(c->qcount + 18);
-      // deferred particles may run behind the stream within this call: the
-      // kernel finds any step's levels in the ring from the slots' origins
-      base.lag_step = c->lag_step;
-      base.lag_j = c->lag_j;
-      base.step0 = n;
-      base.heavy_budget = c->heavy_budget;
-      base.ring_R = c->R;
-      base.slot_i0 = c->dslot_i0;  // kept current by pic_fields_upload, in stream order
-    }
+    mixed_base(c, base);
+    base.step0 = cont ? c->open_step0 : n;
+  } else {
+    memset(&base, 0, sizeof(base));
   }
   for (int64_t j = 0; j < n_steps; ++j) {
     const int64_t s = n + j;
+    const int64_t J = J0 + j;  // the launch's index in the run
     int slots[kMaxOrder + 1];
     int64_t lo, hi;
     step_slots(c, s, slots, &lo, &hi);
@@ -685,29 +787,33 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
       a.halfE = c->half;
       a.halfB = c->half + W + 1;
       a.coef = coef_cur;
-      a.coef_p = j > 0 ? coef_prev : coef_cur;
+      // deferred work of the previous step: from this call's last launch, or
+      // carried from the last call
+      const bool has_prev = j > 0 || cont;
+      a.coef_p = has_prev ? coef_prev : coef_cur;
       if (binned) {
         const int64_t qsz = 7 * c->capacity;
-        if (j > 0) {
+        if (has_prev) {
           int ps[kMaxOrder + 1];
           int64_t plo, phi;
-          step_slots(c, s - 1, ps, &plo, &phi);
+          int rc = step_slots(c, s - 1, ps, &plo, &phi);
+          if (rc != PIC_OK) return rc;
           fill_mixed(c, a, s - 1, plo, phi, true);
         } else {
           fill_mixed(c, a, s, lo, hi, true);  // no deferred work on the first step
         }
-        a.queue_in = c->queue + (j & 1) * qsz;
-        a.queue_out = c->queue + ((j + 1) & 1) * qsz;
-        a.qcount_in = c->qcount + (j & 1) * 8;
-        a.qcount_out = c->qcount + ((j + 1) & 1) * 8;
-        a.parity_cur = (int)(j & 1);
-        a.parity_next = (int)((j + 1) & 1);
+        a.queue_in = c->queue + (J & 1) * qsz;
+        a.queue_out = c->queue + ((J + 1) & 1) * qsz;
+        a.qcount_in = c->qcount + (J & 1) * 8;
+        a.qcount_out = c->qcount + ((J + 1) & 1) * 8;
+        a.parity_cur = (int)(J & 1);
+        a.parity_next = (int)((J + 1) & 1);
         a.finalize = 0;
         e = cudaSuccess;
-        if (predicted && j % c->predict_every == 0) {
+        if (predicted && J % c->predict_every == 0) {
           // refresh the predictions from the state after the previous step and
           // rebuild the predicted queue, which the next predict_every steps
-          // push (a call starts with a refresh: its status bytes carry no
+          // push (a run starts with a refresh: its status bytes carry no
           // queue marks)
           e = cudaMemsetAsync(c->qcount + 32, 0, 8 * sizeof(int32_t), c->stream);
           int ps[kMaxOrder + 1];
@@ -734,24 +840,14 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
           a.pred_queue = c->pred_queue;
           a.pred_count = c->qcount + 32;
         }
+        // the last launch of a carrying call leaves no particle further behind
+        // than the steps whose levels the ring keeps for the next call
+        if (carry && j == n_steps - 1) a.keep_step = s - (c->prm.carry - 1);
         if (e == cudaSuccess) e = mark(ev0);
         if (e == cudaSuccess)
           e = launch_binned_step(a, p, c->sm_count, c->stream, &launches);
-        if (e == cudaSuccess && j == n_steps - 1) {
-          // close the call: finish what the last step deferred, public status bytes
-          PushArgsMixed f = a;
-          fill_mixed(c, f, s, lo, hi, true);
-          f.queue_in = c->queue + (n_steps & 1) * qsz;
-          f.qcount_in = c->qcount + (n_steps & 1) * 8;
-          f.queue_out = c->queue + ((n_steps + 1) & 1) * qsz;
-          f.qcount_out = c->qcount + ((n_steps + 1) & 1) * 8;
-          f.finalize = 1;
-          f.step_cur = s + 1;   // bring every deferred particle to the end of step s
-          f.coef_p = coef_cur;  // the deferred work finishes this (the last) step
-          f.pred_queue = nullptr;
-          f.pred_count = nullptr;
-          e = launch_binned_step(f, p, c->sm_count, c->stream, &launches);
-        }
+        if (e == cudaSuccess && !carry && j == n_steps - 1)
+          e = closing_launch(c, a, s, lo, hi, J, coef_cur, &launches);
       } else {
         e = mark(ev0);
         if (e == cudaSuccess)
@@ -762,6 +858,13 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
     if (e != cudaSuccess) return fail(c, PIC_ECUDA, "push launch: %s", cudaGetErrorString(e));
     if (c->timing) CUDA_TRY(c, cudaEventRecord(ev1, c->stream));
   }
+  if (carry && c->n > 0) {
+    c->open = true;
+    if (!cont) c->open_step0 = n;
+    c->open_last = n + n_steps - 1;
+    c->open_keep = c->open_last - (c->prm.carry - 1);
+    c->run_j = J0 + n_steps;
+  }
   if (stats) return collect_stats(c, stats, true);
   return PIC_OK;
 }
@@ -769,9 +872,11 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
 extern "C" int pic_features(pic_ctx* c, int64_t n, float* phi) {
   if (!c || !phi) return PIC_EINVAL;
   if (c->prm.precision != PIC_MIXED) return fail(c, PIC_EINVAL, "pic_features: needs the mixed form%s");
+  int rc = close_open(c);  // features of whole steps: carried sub-cycles first
+  if (rc != PIC_OK) return rc;
   int slots[kMaxOrder + 1];
   int64_t lo, hi;
-  int rc = step_slots(c, n, slots, &lo, &hi);
+  rc = step_slots(c, n, slots, &lo, &hi);
   if (rc != PIC_OK) return rc;
   PushArgsMixed a;
   memset(&a, 0, sizeof(a));
@@ -791,9 +896,11 @@ extern "C" int pic_features(pic_ctx* c, int64_t n, float* phi) {
 extern "C" int pic_predict(pic_ctx* c, const pic_mlp* mlp, int64_t n, uint8_t* pred) {
   if (!c || !mlp || (!pred && c->n > 0)) return PIC_EINVAL;
   if (c->prm.precision != PIC_MIXED) return fail(c, PIC_EINVAL, "pic_predict: needs the mixed form%s");
+  int rc = close_open(c);  // features of whole steps: carried sub-cycles first
+  if (rc != PIC_OK) return rc;
   int slots[kMaxOrder + 1];
   int64_t lo, hi;
-  int rc = step_slots(c, n, slots, &lo, &hi);
+  rc = step_slots(c, n, slots, &lo, &hi);
   if (rc != PIC_OK) return rc;
   PushArgsMixed a;
   memset(&a, 0, sizeof(a));
@@ -816,6 +923,9 @@ extern "C" int pic_attach_predictor(pic_ctx* c, pic_mlp* mlp, int32_t every) {
   if (c->prm.schedule != PIC_SCHED_PREDICTED)
     return fail(c, PIC_EINVAL, "pic_attach_predictor: the context's schedule is not PIC_SCHED_PREDICTED%s");
   if (every < 1) return fail(c, PIC_EINVAL, "pic_attach_predictor: every must be >= 1%s");
+  // the predicted queue of a carried run belongs to the old predictor
+  int rc = close_open(c);
+  if (rc != PIC_OK) return rc;
   c->mlp = mlp;
   c->predict_every = every;
   return PIC_OK;

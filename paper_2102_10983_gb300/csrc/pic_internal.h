@@ -128,8 +128,12 @@ struct PushArgsMixed {
   // sub-cycles per launch and catches a lagging particle up with the stream.
   int32_t* lag_step;
   uint16_t* lag_j;
-  int64_t step0;          // first macro step of the call
+  int64_t step0;          // base of lag_step: the first step of the call (of the
+                          // first call of a run of carried calls)
   int64_t step_cur;       // this launch's stream step (closing launch: last step + 1)
+  int64_t keep_step;      // a particle may be left out of budget only in a step
+                          // >= keep_step (INT64_MIN: any); below it the budget
+                          // does not apply
   int32_t heavy_budget;   // <= 0: no limit
   int32_t ring_R;         // ring slots (levels at slot level mod R, mirrored at + R)
   const int64_t* slot_i0; // device copy of each slot's window origin

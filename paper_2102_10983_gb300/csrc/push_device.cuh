@@ -679,15 +679,31 @@ __device__ __forceinline__ void load_fields(StepFields<P, RING>& F, const PushAr
 // the same operations, in the same order, as gathering the levels at the
 // particle.  lo, hi: step n's window.  Lost particles and i >= n get zeros;
 // E and B are zero outside the window.
-__device__ __forceinline__ void particle_features(const PushArgsMixed& a, const float* nodeE,
-                                                  const float* nodeB, int32_t lo, int32_t hi,
-                                                  int64_t i, float (&f)[6]) {
+// The stored state particle_features reads (status LOST for i >= n), loaded
+// apart from the arithmetic so that a caller can issue the loads of its next
+// particle before working on the current one.
+struct FeatureInput {
+  uint8_t st;
+  MixedState s;
+};
+__device__ __forceinline__ FeatureInput feature_input(const PushArgsMixed& a, int64_t i) {
+  FeatureInput r;
+  r.st = PIC_STATUS_LOST;
+  r.s = {0, 0.f, 0.f, 0.f, 0.f};
+  if (i < a.n) {
+    r.st = a.status[i];
+    r.s = load_state(a, i);
+  }
+  return r;
+}
+
+__device__ __forceinline__ void features_of(const PushArgsMixed& a, const float* nodeE,
+                                            const float* nodeB, int32_t lo, int32_t hi,
+                                            const FeatureInput& in, float (&f)[6]) {
 #pragma unroll
   for (int q = 0; q < 6; ++q) f[q] = 0.f;
-  if (i >= a.n) return;
-  const uint8_t st = a.status[i];
-  if (st & PIC_STATUS_LOST) return;
-  const MixedState s = load_state(a, i);
+  if (in.st & PIC_STATUS_LOST) return;
+  const MixedState& s = in.s;
   int32_t je, jb;
   float we, wb;
   if (tent_coords(s.cell, s.frac, lo, hi, je, we, jb, wb)) {
@@ -701,6 +717,12 @@ __device__ __forceinline__ void particle_features(const PushArgsMixed& a, const 
   f[3] = asinhf(s.uy);
   f[4] = asinhf(s.uz);
   f[5] = 0.5f * log1pf(norm2(s.ux, s.uy, s.uz));
+}
+
+__device__ __forceinline__ void particle_features(const PushArgsMixed& a, const float* nodeE,
+                                                  const float* nodeB, int32_t lo, int32_t hi,
+                                                  int64_t i, float (&f)[6]) {
+  features_of(a, nodeE, nodeB, lo, hi, feature_input(a, i), f);
 }
 
 // Field view of macro step s from the mirrored ring and the device copy of
@@ -853,7 +875,10 @@ __device__ __forceinline__ void stash_drain(const PushArgsMixed& a, const StepFi
 // spending at most heavy_budget sub-steps of long sub-cycles; then take the
 // criterion of the current step: pushed at once if k < kDeferMin, else
 // deferred again.  Out of budget: the particle stays deferred where it is
-// (offset not normalised) and resumes in the next launch.  finalize: bring it
+// (offset not normalised) and resumes in the next launch -- but not in a step
+// before keep_step (the last launch of a call that carries its deferred work
+// into the next call: the steps whose levels the ring must keep), which it
+// finishes regardless of the budget.  finalize: bring it
 // to the end of the last step only (public status).
 template <int P, bool RING>
 __device__ __forceinline__ void heavy_particle(const PushArgsMixed& a, const StepFields<P, RING>& Fp,
@@ -881,7 +906,7 @@ __device__ __forceinline__ void heavy_particle(const PushArgsMixed& a, const Ste
     // sub-steps j0+1 .. j1 of step si
     const int m = 1 << (2 * k);
     int j1 = m;
-    if (k >= kDeferMin && m - j0 > budget) j1 = j0 + budget;
+    if (k >= kDeferMin && m - j0 > budget && si >= a.keep_step) j1 = j0 + budget;
     bool ok;
     if (si >= a.step_cur - 1) {  // the previous or the current step: node tables
       const StepFields<P, RING> Fs = si == a.step_cur ? Fc : Fp;
@@ -965,7 +990,7 @@ __device__ __forceinline__ void heavy_particle(const PushArgsMixed& a, const Ste
       k_prev = k;
       k = kn;
       j0 = 0;
-      if (k >= kDeferMin && budget <= 0) {
+      if (k >= kDeferMin && budget <= 0 && si >= a.keep_step) {
         store_state(a, i, s);
         defer_mark(a, i, k_prev, k, si);
         defer_key = k;

@@ -119,8 +119,9 @@ extern "C" int pic_push_mixed_noalloc(const pic_params* prm, int64_t n_particles
   if (prm->order < 1 || prm->order > kMaxOrder || prm->k_max < 0 || prm->k_max > kMaxK ||
       (prm->field_time != 0 && prm->field_time != 1))
     return fail(PIC_EINVAL, "pic_push_mixed_noalloc: order 1..5, k_max 0..7, field_time 0/1");
-  if (prm->precision != PIC_MIXED || prm->schedule != PIC_SCHED_BINNED || prm->diagnostics != 0)
-    return fail(PIC_EINVAL, "pic_push_mixed_noalloc: needs precision PIC_MIXED, schedule PIC_SCHED_BINNED, no diagnostics");
+  if (prm->precision != PIC_MIXED || prm->schedule != PIC_SCHED_BINNED || prm->diagnostics != 0 ||
+      prm->carry != 0)
+    return fail(PIC_EINVAL, "pic_push_mixed_noalloc: needs precision PIC_MIXED, schedule PIC_SCHED_BINNED, no diagnostics, carry 0");
   if (n_particles < 0 || n_particles > kNoAllocMaxParticles)
     return fail(PIC_EINVAL, "pic_push_mixed_noalloc: n_particles exceeds the 65,536 the static scratch holds");
   if (n_particles > 0 && (!cell || !frac || !px || !py || !pz || !status))
@@ -170,6 +171,7 @@ extern "C" int pic_push_mixed_noalloc(const pic_params* prm, int64_t n_particles
   };
   PushArgsMixed base;
   memset(&base, 0, sizeof(base));
+  base.keep_step = INT64_MIN;
   base.n = n_particles;
   base.cell = cell; base.frac = frac; base.px = px; base.py = py; base.pz = pz;
   base.status = status;

@@ -32,7 +32,7 @@ class PicParams(ctypes.Structure):
                 ("qm", ctypes.c_double), ("order", ctypes.c_int32), ("k_max", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("field_time", ctypes.c_int32),
                 ("schedule", ctypes.c_int32), ("heavy_budget", ctypes.c_int32),
-                ("diagnostics", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("diagnostics", ctypes.c_int32), ("carry", ctypes.c_int32)]
 
 
 class PicEnsemble(ctypes.Structure):
@@ -110,6 +110,7 @@ SIGNATURES = {
     "pic_fields_upload": (ctypes.c_int, [_VP, _I64, _I64, _VP, _VP, _I32]),
     "pic_push_step": (ctypes.c_int, [_VP, _I64, _I64, ctypes.POINTER(PicStepStats)]),
     "pic_stats_read": (ctypes.c_int, [_VP, ctypes.POINTER(PicStepStats), _I32]),
+    "pic_finish": (ctypes.c_int, [_VP]),
     "pic_set_stream": (ctypes.c_int, [_VP, _VP]),
     "pic_timing_enable": (ctypes.c_int, [_VP, _I32]),
     "pic_timing_read": (ctypes.c_int, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_I64), _I32]),
@@ -229,10 +230,10 @@ class Integrator:
 
     def __init__(self, dt, dx, psi_max, order=3, k_max=7, precision=PIC_FP64, field_time=0,
                  schedule=PIC_SCHED_PLAIN, qm=-1.0, capacity=0, window=256, ring_levels=None,
-                 stream=None, heavy_budget=0, diagnostics=0):
+                 stream=None, heavy_budget=0, diagnostics=0, carry=0):
         self.params = PicParams(float(dt), float(dx), float(psi_max), float(qm), int(order),
                                 int(k_max), int(precision), int(field_time), int(schedule),
-                                int(heavy_budget), int(diagnostics))
+                                int(heavy_budget), int(diagnostics), int(carry))
         self.window = int(window)
         self.ring_levels = int(ring_levels if ring_levels is not None else order + 1)
         self.capacity = int(capacity)
@@ -282,6 +283,9 @@ class Integrator:
                                    ctypes.byref(st) if st is not None else None)
         _check(code, self.ctx, ok=ok)
         return (st, code) if want_stats else (None, code)
+
+    def pic_finish(self):
+        _check(lib().pic_finish(self.ctx), self.ctx)
 
     def pic_stats_read(self, reset=True) -> PicStepStats:
         st = PicStepStats()

@@ -54,6 +54,9 @@ def test_host_side_validation_rejects_bad_parameters():
         native.PicParams(0.1, 1.0, 0.01, -1.0, 3, 7, 0, 0, 1),     # binned needs mixed
         native.PicParams(0.1, 1.0, 0.01, -1.0, 3, 7, 1, 0, 0, 0, native.PIC_DIAG_WORK),  # FP64 only
         native.PicParams(0.1, 1.0, 0.01, -1.0, 3, 7, 0, 0, 0, 0, 2),  # unknown diagnostic
+        native.PicParams(0.1, 1.0, 0.01, -1.0, 3, 7, 1, 0, 0, 0, 0, 1),  # carry, plain schedule
+        native.PicParams(0.1, 1.0, 0.01, -1.0, 3, 7, 1, 0, 1, 0, 0, -1),  # negative carry
+        native.PicParams(0.1, 1.0, 0.01, -1.0, 3, 7, 1, 0, 1, 0, 0, 5),  # ring 8 < 3 + 1 + 5
     ]
     for prm in bad:
         assert L.pic_create(ctypes.byref(prm), 16, 64, 8, None, ctypes.byref(h)) == native.PIC_EINVAL
@@ -62,4 +65,8 @@ def test_host_side_validation_rejects_bad_parameters():
     good = native.PicParams(0.1, 1.0, 0.01, -1.0, 3, 7, 0, 0, 0)
     assert L.pic_create(ctypes.byref(good), 16, 100, 8, None, ctypes.byref(h)) == native.PIC_EINVAL
     assert L.pic_create(ctypes.byref(good), 16, 64, 3, None, ctypes.byref(h)) == native.PIC_EINVAL
+    carried = native.PicParams(0.1, 1.0, 0.01, -1.0, 3, 7, 1, 0, 1, 0, 0, 2)
+    assert L.pic_create(ctypes.byref(carried), 16, 64, 5, None, ctypes.byref(h)) == native.PIC_EINVAL
+    assert b"carry" in L.pic_last_error(None)
+    assert L.pic_finish(None) == native.PIC_EINVAL
     assert L.pic_destroy(None) == native.PIC_OK
