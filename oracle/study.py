@@ -33,14 +33,15 @@ class TrjResult(ctypes.Structure):
     _fields_ = [("eps_dephasing", ctypes.c_double), ("eps_energy", ctypes.c_double),
                 ("gamma_max", ctypes.c_double), ("n_steps", ctypes.c_int64),
                 ("n_star", ctypes.c_int64), ("substeps", ctypes.c_int64),
-                ("k_hist", ctypes.c_int64 * 8)]
+                ("k_hist", ctypes.c_int64 * 8), ("x", ctypes.c_double), ("px", ctypes.c_double),
+                ("py", ctypes.c_double), ("pz", ctypes.c_double)]
 
     def as_dict(self):
         n, ns = self.n_steps, self.n_star
         return {"eps_dephasing": self.eps_dephasing, "eps_energy": self.eps_energy,
                 "gamma_max": self.gamma_max, "N": n, "N_star": ns,
                 "delta_steps": ns / (ns + n) if n + ns else 0.0, "substeps": self.substeps,
-                "k_hist": list(self.k_hist)}
+                "k_hist": list(self.k_hist), "final": (self.x, self.px, self.py, self.pz)}
 
 
 def _lib():

@@ -17,7 +17,7 @@
  *                   gamma_th = 1 + a(xi_p)^2 / 2 at the momentum's phase
  *                   xi_p = t_p - x_p, t_p = t_{n+1} - h/2, x_p = x - (h/2) v_x;
  *   gamma_max, N (macro steps), N* (sub-steps of macro steps with k > 0), the
- *   k histogram.
+ *   k histogram, and the final position and momentum.
  */
 #include <math.h>
 #include <stdint.h>
@@ -35,6 +35,7 @@ typedef struct {
   double eps_dephasing, eps_energy, gamma_max;
   int64_t n_steps, n_star, substeps;
   int64_t k_hist[8];
+  double x, px, py, pz; /* the state after the last macro step */
 } trj_result;
 
 static double trj_a(const trj_params* q, double xi) {
@@ -154,4 +155,8 @@ void trj_run(const trj_params* q, trj_result* r) {
     if (g > r->gamma_max) r->gamma_max = g;
   }
   r->n_steps = q->n_steps;
+  r->x = xi;
+  r->px = pv[0];
+  r->py = pv[1];
+  r->pz = pv[2];
 }

@@ -36,9 +36,11 @@ def run_oracle(wl: Workload, prm: oracle.Params, parts: oracle.Particles, n0: in
 
 def run_oracle_follow(wl: Workload, prm: oracle.Params, parts: oracle.Particles, n0: int,
                       n_steps: int, chunk: int = 48, margin: int = 6, r_ref=None, r_dev=None,
-                      stats=None, on_chunk=None, work=None) -> oracle.OrcStats:
+                      stats=None, on_chunk=None, work=None,
+                      field_scale: float = 1.0) -> oracle.OrcStats:
     """Like run_oracle, with a small window that follows the particles (all
-    levels of a chunk share one origin; particles move < 1 node per step)."""
+    levels of a chunk share one origin; particles move < 1 node per step).
+    field_scale multiplies every field sample (a perturbation of the inputs)."""
     p = prm.order
     st = stats if stats is not None else oracle.OrcStats()
     done = 0
@@ -53,6 +55,8 @@ def run_oracle_follow(wl: Workload, prm: oracle.Params, parts: oracle.Particles,
         i0 = np.full(c + p, lo, dtype=np.int64)
         from paper_2102_10983_gb300.workloads import sample_levels
         E, B = sample_levels(wl.wave, wl.dt, wl.dx, n - p, c + p, i0, W, rowwise=False)
+        if field_scale != 1.0:
+            E, B = E * field_scale, B * field_scale
         oracle.run(prm, parts, E, i0, B, i0, st, r_ref, r_dev, work)
         done += c
         if on_chunk is not None:

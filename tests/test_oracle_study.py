@@ -101,3 +101,44 @@ def test_delta_steps_falls_with_a0_and_with_resolution(scan):
         assert d75 > d150 > d300
         d3, d5 = scan[(a0, 3, 0.01, 75)]["delta_steps"], scan[(a0, 5, 0.01, 75)]["delta_steps"]
         assert abs(d5 - d3) < 0.15 * d3, (a0, d3, d5)
+
+
+def test_study_oracle_agrees_with_the_push_oracle():
+    """The study oracle (fields sampled from the formula as the gather needs
+    them) against the push oracle of the rest of the suite (pinned by
+    tests/test_oracle_pins.py; fields uploaded as levels of a window that
+    follows the electron) on the same run: a0 = 10, third order with
+    sub-cycling, lambda/75, one electron from rest through the whole pulse.
+    The two restate Algorithm 1 separately and round the field samples
+    differently.  Every step's k must agree; the final state may differ by no
+    more than four times what moving every field sample of the push oracle
+    by 1 or 4 units in the last place does (the run amplifies a one-ulp field
+    change to ~3e-5 in x: rounding, not a difference of method, which would
+    show as a much larger gap or other k)."""
+    import oracle
+    import _harness as H
+    from paper_2102_10983_gb300 import workloads as W
+
+    a0, res = 10.0, 75
+    q = study.params(a0, 3, 0.01, res)
+    r = study.run([q])[0]
+    wl = W.Workload(name="study_pin", n_particles=1, a0=a0, dt=q.dt, dx=q.dx, psi_max=0.01,
+                    order=3, n_steps=q.n_steps, x_lo=0.0, x_hi=0.0, profile="gauss",
+                    xi0=q.xi0, sigma=q.sigma)
+    prm = oracle.Params(dt=q.dt, dx=q.dx, psi_max=0.01, order=3)
+
+    def push(scale):
+        parts = oracle.Particles([0.0], [0.0], [0.0], [0.0])
+        st = H.run_oracle_follow(wl, prm, parts, 0, q.n_steps, field_scale=scale)
+        return st, (parts.x[0], parts.px[0], parts.py[0], parts.pz[0])
+
+    st, ref = push(1.0)
+    assert list(st.k_hist)[:8] == r["k_hist"] and not any(list(st.k_hist)[8:])
+    assert r["k_hist"][2] > 0, "the run must sub-cycle"
+    spread = [0.0] * 4
+    for u in (1, -1, 4, -4):
+        _, v = push(1.0 + u * 2.0 ** -52)
+        spread = [max(s_, abs(a - b)) for s_, a, b in zip(spread, v, ref)]
+    for q_, (a, b) in enumerate(zip(r["final"], ref)):
+        assert abs(a - b) <= 4.0 * spread[q_] + 1e-300, (q_, a - b, spread[q_])
+    assert ref[0] > 100.0  # pushed forward through the pulse
