@@ -26,7 +26,8 @@ class TrjParams(ctypes.Structure):
                 ("dt", ctypes.c_double), ("dx", ctypes.c_double), ("psi_max", ctypes.c_double),
                 ("qm", ctypes.c_double), ("order", ctypes.c_int32), ("k_max", ctypes.c_int32),
                 ("field_time", ctypes.c_int32), ("pad", ctypes.c_int32),
-                ("n_steps", ctypes.c_int64), ("x0", ctypes.c_double)]
+                ("n_steps", ctypes.c_int64), ("x0", ctypes.c_double),
+                ("field_scale", ctypes.c_double)]
 
 
 class TrjResult(ctypes.Structure):
@@ -58,11 +59,12 @@ def n_steps_for(a0: float, dt: float) -> int:
 
 
 def params(a0: float, order: int, psi_max: float, res: float, k_max: int = 7,
-           field_time: int = 0) -> TrjParams:
-    """One run: lambda/(c dt) = res, c dt/dx = 0.99; psi_max = inf: no sub-cycling."""
+           field_time: int = 0, field_scale: float = 1.0) -> TrjParams:
+    """One run: lambda/(c dt) = res, c dt/dx = 0.99; psi_max = inf: no sub-cycling.
+    field_scale multiplies every field sample (a perturbation of the inputs)."""
     dt = 2 * math.pi / res
     return TrjParams(a0, XI0, SIGMA, dt, dt / 0.99, psi_max, -1.0, order, k_max, field_time, 0,
-                     n_steps_for(a0, dt), 0.0)
+                     n_steps_for(a0, dt), 0.0, field_scale)
 
 
 def run(cases, threads: int = 8):

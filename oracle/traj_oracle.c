@@ -29,6 +29,8 @@ typedef struct {
   int32_t order, k_max, field_time, pad;
   int64_t n_steps;
   double x0;
+  double field_scale; /* multiplies every field sample (1: the pulse as given;
+                         tests move it by a few ulps to measure sensitivity) */
 } trj_params;
 
 typedef struct {
@@ -47,7 +49,7 @@ static double trj_a(const trj_params* q, double xi) {
 static double trj_field(const trj_params* q, double xi) {
   const double d = xi - q->xi0;
   const double env = exp(-(d * d) / (2.0 * q->sigma * q->sigma));
-  return -(q->a0 * env * (cos(xi) - (d / (q->sigma * q->sigma)) * sin(xi)));
+  return -(q->a0 * env * (cos(xi) - (d / (q->sigma * q->sigma)) * sin(xi))) * q->field_scale;
 }
 
 static void trj_lagrange(int p, int is_e, double theta, double* w) {

@@ -4,8 +4,8 @@
 // the field sampled on the grid (the "perfectly propagating PIC" of Sec. III):
 // E_y at nodes i dx and times n dt, B_z at (i + 1/2) dx and (n + 1/2) dt.
 //
-// One CTA per case (a0, dt, dx, Psi_max, order, ...), one thread per electron
-// of the case, x0 = j lambda / n_electrons; each thread integrates its whole
+// One thread per electron of a case (a0, dt, dx, Psi_max, order, ...), one
+// warp per CTA, x0 = j lambda / n_electrons; each thread integrates its whole
 // trajectory with the method (Algorithm 1 of Sec. IV, order-p Lagrange in
 // time of Sec. VI, tent in space, Boris), in FP64 compiled with -fmad=false in
 // the order of a serial evaluation.  The field values a gather needs are
@@ -38,15 +38,27 @@ __device__ __forceinline__ double a_of(const pic_study_case& q, double xi) {
 __device__ __forceinline__ double field_of(const pic_study_case& q, double xi) {
   const double d = xi - q.xi0;
   const double env = exp(-(d * d) / (2.0 * q.sigma * q.sigma));
-  return -(q.a0 * env * (cos(xi) - (d / (q.sigma * q.sigma)) * sin(xi)));
+  double sn, cs;
+  sincos(xi, &sn, &cs);  // one argument reduction for both
+  return -(q.a0 * env * (cs - (d / (q.sigma * q.sigma)) * sn));
 }
 
-__device__ void lagrange(int p, bool is_e, double theta, double* w) {
+// The rounded reciprocals of the integer denominators prod_{k != j} (j - k),
+// formed once per electron (the same values the weights' definition rounds).
+__device__ void lagrange_inv_den(int p, double* inv_den) {
+  for (int j = 0; j <= p; ++j) {
+    long long den = 1;
+    for (int k = 0; k <= p; ++k)
+      if (k != j) den *= (long long)(j - k);
+    inv_den[j] = 1.0 / (double)den;
+  }
+}
+
+__device__ void lagrange(int p, bool is_e, double theta, const double* inv_den, double* w) {
   const double c_off = is_e ? -0.5 : -1.0;
   for (int j = 0; j <= p; ++j) {
     double num = 1.0;
     bool first = true;
-    long long den = 1;
     for (int k = 0; k <= p; ++k) {
       if (k == j) continue;
       const double factor = ((double)(p - k) + c_off) + theta;
@@ -56,9 +68,8 @@ __device__ void lagrange(int p, bool is_e, double theta, double* w) {
       } else {
         num = num * factor;
       }
-      den *= (long long)(j - k);
     }
-    w[j] = num * (1.0 / (double)den);
+    w[j] = num * inv_den[j];
   }
 }
 
@@ -122,8 +133,9 @@ __device__ void study_electron(const pic_study_case& q, double x0, double* out_e
                                double* out_eps_e, double* out_gmax, int64_t* n_star,
                                int64_t* substeps, int64_t* k_hist) {
   const double dt = q.dt, inv_dx = 1.0 / q.dx;
-  double wB_half[P + 1], wE[P + 1], wB[P + 1];
-  lagrange(P, false, 0.5, wB_half);
+  double wB_half[P + 1], wE[P + 1], wB[P + 1], inv_den[P + 1];
+  lagrange_inv_den(P, inv_den);
+  lagrange(P, false, 0.5, inv_den, wB_half);
   GridCache<P> cE, cB;
   double pv0 = 0.0, pv1 = 0.0, pv2 = 0.0;
   double xi = x0;
@@ -151,8 +163,8 @@ __device__ void study_electron(const pic_study_case& q, double x0, double* out_e
     for (int64_t j = 1; j <= m; ++j) {
       const double theta = (q.field_time == 0) ? 0.5 + (double)(j - 1) * inv_m
                                                 : ((double)(j - 1) + 0.5) * inv_m;
-      lagrange(P, true, theta, wE);
-      lagrange(P, false, theta, wB);
+      lagrange(P, true, theta, inv_den, wE);
+      lagrange(P, false, theta, inv_den, wB);
       s = xi * inv_dx;
       const double ey = gather<P>(cE, q, false, n, wE, s);
       const double bz = gather<P>(cB, q, true, n, wB, s - 0.5);
@@ -199,17 +211,28 @@ struct StudyAcc {
   unsigned long long k_hist[8];
 };
 
-template <int P>
-__global__ void __launch_bounds__(256) study_kernel(const pic_study_case* cases, pic_study_result* out,
-                                                    StudyAcc* acc) {
-  const pic_study_case q = cases[blockIdx.x];
-  if ((int)threadIdx.x >= q.n_electrons || q.order != P) return;
-  const double x0 = (2.0 * M_PI) * (double)threadIdx.x / (double)q.n_electrons;
+// One warp per CTA: block b runs electrons 32 (b % per_case) .. + 31 of case
+// b / per_case, so a case of 64 electrons spreads over two SMs (the FP64 pipe
+// of one SM is the bound: ~2 DFMA per clock); every order in one launch, so
+// the cases of all orders run at once.
+__global__ void __launch_bounds__(32) study_kernel(const pic_study_case* cases, pic_study_result* out,
+                                                   StudyAcc* acc, int per_case) {
+  const int c = blockIdx.x / per_case;
+  const pic_study_case q = cases[c];
+  const int e = (blockIdx.x % per_case) * 32 + (int)threadIdx.x;
+  if (e >= q.n_electrons) return;
+  const double x0 = (2.0 * M_PI) * (double)e / (double)q.n_electrons;
   double er, ee, gm;
   int64_t ns, sub;
   int64_t kh[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  study_electron<P>(q, x0, &er, &ee, &gm, &ns, &sub, kh);
-  StudyAcc& A = acc[blockIdx.x];
+  switch (q.order) {
+    case 1: study_electron<1>(q, x0, &er, &ee, &gm, &ns, &sub, kh); break;
+    case 2: study_electron<2>(q, x0, &er, &ee, &gm, &ns, &sub, kh); break;
+    case 3: study_electron<3>(q, x0, &er, &ee, &gm, &ns, &sub, kh); break;
+    case 4: study_electron<4>(q, x0, &er, &ee, &gm, &ns, &sub, kh); break;
+    default: study_electron<5>(q, x0, &er, &ee, &gm, &ns, &sub, kh); break;
+  }
+  StudyAcc& A = acc[c];
   atomic_max_pos(&A.eps_r, er);
   atomic_max_pos(&A.eps_e, ee);
   atomic_max_pos(&A.gmax, gm);
@@ -217,8 +240,8 @@ __global__ void __launch_bounds__(256) study_kernel(const pic_study_case* cases,
   atomicAdd(&A.substeps_sum, (unsigned long long)sub);
   for (int k = 0; k < 8; ++k)
     if (kh[k]) atomicAdd(&A.k_hist[k], (unsigned long long)kh[k]);
-  if (threadIdx.x == 0) {
-    pic_study_result& r = out[blockIdx.x];
+  if (e == 0) {
+    pic_study_result& r = out[c];
     r.eps_dephasing_first = er;
     r.eps_energy_first = ee;
     r.gamma_max_first = gm;
@@ -266,18 +289,13 @@ extern "C" int pic_study_run(const pic_study_case* cases, int32_t n_cases, pic_s
   e = cudaMemcpyAsync(dcases, cases, sizeof(pic_study_case) * n_cases, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(dacc, 0, sizeof(StudyAcc) * n_cases, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(dout, 0, sizeof(pic_study_result) * n_cases, st);
-  // one launch per order present (each CTA skips the cases of other orders)
-  bool present[kMaxOrder + 1] = {};
-  for (int32_t i = 0; i < n_cases; ++i) present[cases[i].order] = true;
-  for (int p = 1; p <= kMaxOrder && e == cudaSuccess; ++p) {
-    if (!present[p]) continue;
-    switch (p) {
-      case 1: study_kernel<1><<<n_cases, 256, 0, st>>>(dcases, dout, dacc); break;
-      case 2: study_kernel<2><<<n_cases, 256, 0, st>>>(dcases, dout, dacc); break;
-      case 3: study_kernel<3><<<n_cases, 256, 0, st>>>(dcases, dout, dacc); break;
-      case 4: study_kernel<4><<<n_cases, 256, 0, st>>>(dcases, dout, dacc); break;
-      case 5: study_kernel<5><<<n_cases, 256, 0, st>>>(dcases, dout, dacc); break;
-    }
+  int per_case = 1;
+  for (int32_t i = 0; i < n_cases; ++i) {
+    const int w = (cases[i].n_electrons + 31) / 32;
+    per_case = w > per_case ? w : per_case;
+  }
+  if (e == cudaSuccess) {
+    study_kernel<<<(unsigned)(n_cases * per_case), 32, 0, st>>>(dcases, dout, dacc, per_case);
     e = cudaGetLastError();
   }
   std::vector<StudyAcc> acc(n_cases);

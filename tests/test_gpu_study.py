@@ -4,8 +4,13 @@ against the study oracle (oracle/study.py).
 Both evaluate the same method on the same sampled pulse in FP64 in the same
 operation order; the field samples come from the device's exp/sin/cos on one
 side and the C library's on the other, so the two differ by the propagation of
-last-bit differences: the dephasing and energy errors must agree to 1e-7
-relative and the sub-step counts exactly (no decision of the criterion flips).
+last-bit differences, which these runs amplify (a one-ulp change of every
+field sample moves eps_dephasing of a0 = 10, lambda/75 by ~1e-5 relative).
+At a0 = 25 they are chaotic: a one-ulp change flips the criterion's k at some
+steps and moves eps by tens of percent.  So the errors, gamma_max and N* must
+agree to within four times the spread the oracle itself shows when every
+field sample is moved by 1 or 4 ulps (N* exactly where that spread is zero,
+as at a0 = 10).
 An ensemble of electrons over a wavelength bounds electron 0's errors from
 above and keeps the paper's claim (order 3 + sub-cycling below 0.1).
 """
@@ -28,14 +33,25 @@ CASES = [dict(a0=a0, order=o, psi_max=ps, res=res)
                                                        (3, 1e30, 75), (5, 0.01, 75), (3, 0.01, 150))]
 
 
+ULP = 2.0 ** -52
+
+
 def test_study_matches_oracle_on_electron_zero():
     gpu = native.study_run([dict(c, n_electrons=1) for c in CASES])
-    ref = study.run([study.params(c["a0"], c["order"], c["psi_max"], c["res"]) for c in CASES])
-    for c, g, r in zip(CASES, gpu, ref):
+    scales = (1.0, 1.0 + ULP, 1.0 - ULP, 1.0 + 4 * ULP, 1.0 - 4 * ULP)
+    runs = study.run([study.params(c["a0"], c["order"], c["psi_max"], c["res"], field_scale=f)
+                      for c in CASES for f in scales])
+    for q, (c, g) in enumerate(zip(CASES, gpu)):
+        r, moved = runs[q * len(scales)], runs[q * len(scales) + 1:(q + 1) * len(scales)]
         assert g["N"] == r["N"]
-        assert g["N_star_first"] == r["N_star"], (c, g["N_star_first"], r["N_star"])
+        # N* is exact unless the oracle's own perturbed runs flip decisions too
+        # (a0 = 25: a one-ulp field change already moves the k of some steps)
+        n_spread = max(abs(m["N_star"] - r["N_star"]) for m in moved)
+        assert abs(g["N_star_first"] - r["N_star"]) <= 4 * n_spread, (c, g["N_star_first"], r["N_star"])
         for key in ("eps_dephasing", "eps_energy", "gamma_max"):
-            assert abs(g[key + "_first"] - r[key]) <= 1e-7 * abs(r[key]), (c, key, g, r)
+            spread = max(abs(m[key] - r[key]) for m in moved)
+            tol = 4.0 * spread + 1e-13 * abs(r[key])
+            assert abs(g[key + "_first"] - r[key]) <= tol, (c, key, g[key + "_first"], r[key], spread)
 
 
 def test_study_ensemble_bounds_electron_zero_and_keeps_the_claim():
