@@ -190,8 +190,11 @@ int pic_work_read(pic_ctx* ctx, double* work, int64_t n, int32_t where);
 /* With pic_params.carry: finish every long sub-cycle carried from the last
  * call (one closing launch, queued on the stream) and return the status bytes
  * to their public form.  Needs the levels of the carried steps, which
- * pic_fields_upload keeps.  No-op when nothing is carried (any schedule or
- * form).  Errors: PIC_EINVAL, PIC_ECUDA. */
+ * pic_fields_upload keeps.  With carry >= 2 a particle left behind the last
+ * step still takes the criterion of the steps it catches up with: those
+ * counts (k histogram, sub-steps) go to the counters that the next
+ * pic_stats_read, or pic_push_step with stats, returns.  No-op when nothing
+ * is carried (any schedule or form).  Errors: PIC_EINVAL, PIC_ECUDA. */
 int pic_finish(pic_ctx* ctx);
 
 /* Read (and optionally reset) the accumulated counters.  Synchronizes. */

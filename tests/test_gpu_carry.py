@@ -42,6 +42,18 @@ def _make(wl, schedule, call_lens, carry=0, heavy_budget=0, order=3):
     return integ
 
 
+def _add(agg, st):
+    """agg += st (the counters the closing launch of pic_finish or of a read
+    adds: the criteria of steps that carried particles still had to take)."""
+    for k in range(8):
+        agg.k_hist[k] += st.k_hist[k]
+    agg.substeps += st.substeps
+    agg.n_star += st.n_star
+    agg.clamped += st.clamped
+    agg.out_of_window += st.out_of_window
+    return agg
+
+
 def _same(a, sa, b, sb):
     for u, v in zip(a, b):
         np.testing.assert_array_equal(u, v)
@@ -75,6 +87,7 @@ def test_carried_calls_are_bitwise_plain(call_lens, carry, budget):
     integ = _make(wl, native.PIC_SCHED_BINNED, call_lens, carry=carry, heavy_budget=budget)
     sb = H.run_gpu_calls(integ, wl, 3, 0, 1000, call_lens)
     b = integ.read_numpy()  # finishes the carried sub-cycles first
+    _add(sb, integ.pic_stats_read(reset=True))
     integ.close()
     assert sa.k_hist[5] > 0, "the front must reach the electrons"
     _same(a, sa, b, sb)
@@ -91,6 +104,7 @@ def test_carried_predicted_schedule_is_bitwise_plain(every):
     integ.attach_predictor(net, every)
     sb = H.run_gpu_calls(integ, wl, 3, 0, 900, [1])
     b = integ.read_numpy()
+    _add(sb, integ.pic_stats_read(reset=True))
     integ.close()
     net.close()
     assert sa.k_hist[5] > 0
@@ -110,12 +124,9 @@ def test_reads_in_the_middle_finish_and_the_run_continues():
     integ.pic_finish()
     integ.pic_finish()  # nothing carried: a no-op
     b = integ.read_numpy()
+    sb = _add(_add(native.PicStepStats(), s1), s2)
+    _add(sb, integ.pic_stats_read(reset=True))
     integ.close()
-    sb = native.PicStepStats()
-    for k in range(8):
-        sb.k_hist[k] = s1.k_hist[k] + s2.k_hist[k]
-    sb.substeps, sb.n_star = s1.substeps + s2.substeps, s1.n_star + s2.n_star
-    sb.clamped, sb.out_of_window = s1.clamped + s2.clamped, s1.out_of_window + s2.out_of_window
     _same(a, sa, b, sb)
 
 
@@ -131,6 +142,7 @@ def test_new_particles_drop_carried_work():
     integ.pic_particles_write(ini.x, ini.px, ini.py, ini.pz)
     sb = H.run_gpu_calls(integ, wl, 3, 0, 600, [1])
     b = integ.read_numpy()
+    _add(sb, integ.pic_stats_read(reset=True))
     integ.close()
     _same(a, sa, b, sb)
 
