@@ -302,6 +302,7 @@ def run_batched(args, dev, stream, sms):
     ms = 0.0
     k_hist = [0] * 8
     substeps = out_of_window = 0
+    calls = []
     for s0 in range(0, K, C):
         n = min(C, K - s0)
         fill(s0 + n + 3)
@@ -311,6 +312,8 @@ def run_batched(args, dev, stream, sms):
         e1.record(stream)
         torch.cuda.synchronize()
         ms += e0.elapsed_time(e1)
+        calls.append({"steps": [s0, s0 + n - 1], "ms_per_step": e0.elapsed_time(e1) / n,
+                      "k_hist": list(st.k_hist)})
         k_hist = [u + v for u, v in zip(k_hist, st.k_hist)]
         substeps += st.substeps
         out_of_window += st.out_of_window
@@ -327,7 +330,7 @@ def run_batched(args, dev, stream, sms):
            "ms_per_step": ms / K, "autotuned": {"chunk": chunk, "blocks_per_sm": blocks,
                                                  "trial_ms_per_step": tune_ms},
            "graph_captured": True, "gpu_launches": b.launches() - launches0,
-           "k_hist": k_hist, "out_of_window": out_of_window, "clocks": clk,
+           "k_hist": k_hist, "out_of_window": out_of_window, "clocks": clk, "calls": calls,
            "roofline": {"bound": "alu", "achieved": ops, "peak": peak, "unit": "FP32 ops/s",
                         "frac": ops / peak,
                         "model": f"{F32_OPS_PER_SUBSTEP} FP32 instructions per Boris sub-step; peak "
@@ -850,11 +853,11 @@ def main():
     # p 3 x f32 + status u8, read and written
     bytes_per = 2 * (4 + 4 + 12 + 1)
     # DRAM bytes (read + write) per electron-step of the push kernel, from one ncu
-    # capture (dram__bytes_read.sum + dram__bytes_write.sum = 184.7 + 166.1 MB) of an
-    # 8,388,608-electron launch at step 2454 of this workload; traffic grows with
+    # capture (dram__bytes_read.sum + dram__bytes_write.sum = 178.9 + 150.5 MB) of an
+    # 8,388,608-electron launch at step 2403 of this workload; traffic grows with
     # the electron count, so it is scaled to the launch timed here.  Re-measure
     # whenever the kernel changes.
-    traffic_per = (184.7e6 + 166.1e6) / 8388608
+    traffic_per = (178.889472e6 + 150.492160e6) / 8388608
     kern_ms = out["learned"]["kern_ms"] if "learned" in out else out["kern_ms"]
     achieved = bytes_per * wl.n_particles / (kern_ms / 1e3) / 1e9
     headline = out.get("learned", {"value": out["value"], "ms_per_step": out["ms_per_step"]})

@@ -68,8 +68,10 @@ extern "C" {
                                  attached predictor (pic_attach_predictor) expects
                                  to take a long sub-cycle (k >= 3) are binned by
                                  predicted k and pushed first (shorter ones are
-                                 left to the stream's in-warp compaction); the
-                                 criterion still decides every k               */
+                                 left to the stream's in-warp compaction); a
+                                 particle that sees no field is predicted k = 0
+                                 without the network; the criterion still
+                                 decides every k                               */
 
 /* per-particle status byte: low 7 bits = k of the last macro step; bit 7 set =
    the particle left the field window and is frozen */

@@ -6,7 +6,10 @@
 //
 // Per CTA (128 threads, one warpgroup) and tile of 128 particles:
 //   features: each thread forms one particle's phi (6 values, BF16, zero-
-//     padded to K = 16) and stores it as row r of A1 [128 x 16];
+//     padded to K = 16) and stores it as row r of A1 [128 x 16], which shares
+//     its bytes with the start of A2 (layer 1 has read A1 before epilogue 1
+//     writes A2, and the next tile's features are stored after layer 3 has
+//     read A2);
 //   layer 1: one tcgen05.mma M=128 N=64 K=16, A1 x W1^T -> D1 (TMEM cols 0..63);
 //   epilogue 1: each warp reads its 32 TMEM lanes (rows) with tcgen05.ld, adds
 //     b1, applies ReLU, rounds to BF16 and writes A2 [128 x 64];
@@ -15,8 +18,8 @@
 //   epilogue 2: b2, ReLU, BF16 -> A2 again (layer 2 has read it);
 //   layer 3: four MMAs A2 x W3^T (N = 16, rows 8..15 of W3 zero) -> D3 (cols 0..15);
 //   epilogue 3: b3, argmax over the 8 classes (ties: the smaller k).
-// A CTA holds 64 TMEM columns and ~33 KB of shared memory, so six CTAs (24
-// warps, six tiles in flight) share an SM: the chain of a tile (features,
+// A CTA holds 64 TMEM columns and ~30 KB of shared memory, so seven CTAs (28
+// warps, seven tiles in flight) share an SM: the chain of a tile (features,
 // three MMA round trips, three epilogues) is latency-bound, the SM is kept
 // busy by the other tiles.
 // One thread issues the MMAs and commits them to an mbarrier that every
@@ -48,17 +51,21 @@ struct TcSmem {
   __align__(1024) unsigned char W1[kTcH * 16 * 2];    // [64 x 16]
   __align__(1024) unsigned char W2[kTcH * kTcH * 2];  // [64 x 64]
   __align__(1024) unsigned char W3[16 * kTcH * 2];    // [16 x 64], rows 8..15 zero
-  __align__(1024) unsigned char A1[kTcTiles][kTcRows * 16 * 2];    // [128 x 16] per tile
-  __align__(1024) unsigned char A2[kTcTiles][kTcRows * kTcH * 2];  // [128 x 64] per tile
+  // [128 x 64] per tile; its first 4 KB are also A1 [128 x 16] (layer 1's input)
+  __align__(1024) unsigned char A2[kTcTiles][kTcRows * kTcH * 2];
   float b1[kTcH], b2[kTcH], b3[kTcOut];
   __align__(8) uint64_t bar;
   uint32_t tmem;
   int failed;
 };
-// Reserved per CTA so that at most six CTAs share an SM: six 64-column TMEM
-// allocations fit its 512 columns, so an allocation never waits.
-constexpr size_t kTcSmemBytes = 37 * 1024;
-static_assert(sizeof(TcSmem) + 1024 <= kTcSmemBytes, "tile buffers fit the reservation");
+// Reserved per CTA (with the slack for aligning the buffers to 1 KB): seven
+// CTAs fit an SM's 228 KB of shared memory and no more, and seven 64-column
+// TMEM allocations fit its 512 columns, so an allocation never waits.
+constexpr int kTcCtasPerSm = 7;
+constexpr size_t kTcSmemBytes = sizeof(TcSmem) + 1024;
+static_assert(kTcCtasPerSm * (kTcSmemBytes + 1024) <= 228 * 1024, "seven CTAs fit shared memory");
+static_assert(8 * (kTcSmemBytes + 1024) > 228 * 1024, "an eighth CTA does not: TMEM stays within 512 columns");
+static_assert(kTcCtasPerSm * kTmemCols <= 512, "TMEM columns of the resident CTAs");
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -163,7 +170,8 @@ __device__ void tc_load_weights(TcSmem& s, const float* P) {
   if (threadIdx.x < kTcOut) s.b3[threadIdx.x] = b3[threadIdx.x];
 }
 
-// Row r of tile q's A1 from this thread's features (BF16, columns 6..15 zero).
+// Row r of tile q's A1 (the start of A2) from this thread's features (BF16,
+// columns 6..15 zero).
 __device__ __forceinline__ void put_features(TcSmem& s, int q, int r, const float (&f)[6]) {
   uint4 lo, hi;
   lo.x = bf2(f[0], f[1]);
@@ -171,8 +179,8 @@ __device__ __forceinline__ void put_features(TcSmem& s, int q, int r, const floa
   lo.z = bf2(f[4], f[5]);
   lo.w = 0u;
   hi = make_uint4(0u, 0u, 0u, 0u);
-  *reinterpret_cast<uint4*>(s.A1[q] + cm_off(r, 0, 16)) = lo;
-  *reinterpret_cast<uint4*>(s.A1[q] + cm_off(r, 8, 16)) = hi;
+  *reinterpret_cast<uint4*>(s.A2[q] + cm_off(r, 0, 16)) = lo;
+  *reinterpret_cast<uint4*>(s.A2[q] + cm_off(r, 8, 16)) = hi;
 }
 
 // Hidden layer epilogue: accumulator columns [c0, c0 + 64) of row r, plus
@@ -212,7 +220,7 @@ __device__ __forceinline__ int tc_tiles(TcSmem& s, const float (&f)[6], uint32_t
   if (ok && threadIdx.x == 0) {
 #pragma unroll
     for (int t = 0; t < kTcTiles; ++t)
-      mma_bf16(s.tmem + kTileCols * t, sdesc(saddr(s.A1[t]), 128, 256), sdesc(saddr(s.W1), 128, 256),
+      mma_bf16(s.tmem + kTileCols * t, sdesc(saddr(s.A2[t]), 128, 256), sdesc(saddr(s.W1), 128, 256),
                idesc_bf16(kTcRows, kTcH), 0);
     mma_commit(&s.bar);
   }
@@ -307,7 +315,8 @@ __device__ __forceinline__ void tc_end(TcSmem& s) {
 // feature nodes; the same code as the features kernel) and the network's
 // class, in one pass.
 template <int P>
-__global__ void __launch_bounds__(kTcThreads) predict_tc_kernel(PushArgsMixed a, const float* Pm, uint8_t* pred) {
+__global__ void __launch_bounds__(kTcThreads) predict_tc_kernel(PushArgsMixed a, const float* Pm, uint8_t* pred,
+                                                                int fieldless_zero) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   TcSmem& s = *reinterpret_cast<TcSmem*>(smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023));
   tc_begin(s, Pm);
@@ -323,7 +332,11 @@ __global__ void __launch_bounds__(kTcThreads) predict_tc_kernel(PushArgsMixed a,
     const FeatureInput nxt = feature_input(a, tn < n_groups ? tn * kTcThreads + threadIdx.x : a.n);
     float f[6];
     features_of(a, a.halfE, a.halfB, a.lo, a.hi, cur, f);
-    const int c = tc_tiles(s, f, ph);
+    // no field at the particle: no rotation, the criterion takes k = 0
+    const bool fieldless = fieldless_zero && f[0] == 0.f && f[1] == 0.f;
+    int c = 0;
+    if (__syncthreads_or(!fieldless)) c = tc_tiles(s, f, ph);  // uniform over the CTA
+    if (fieldless && c != 0xFF) c = 0;
     if (i < a.n) pred[i] = (uint8_t)c;
     if (s.failed) break;
     cur = nxt;
@@ -356,7 +369,7 @@ __global__ void __launch_bounds__(kTcThreads) mlp_infer_tc_kernel(const float* P
 
 static int tc_grid(int64_t n, int sm_count) {
   const int64_t groups = (n + kTcThreads - 1) / kTcThreads;
-  const int64_t cap = (int64_t)(sm_count > 0 ? sm_count : 152) * 6;
+  const int64_t cap = (int64_t)(sm_count > 0 ? sm_count : 152) * kTcCtasPerSm;
   return (int)(groups < cap ? groups : cap);
 }
 
@@ -366,16 +379,17 @@ static cudaError_t tc_configure(K kernel) {
 }
 
 cudaError_t launch_predict_fused(const PushArgsMixed& a, int order, const float* P, uint8_t* pred,
-                                 int sm_count, cudaStream_t st) {
+                                 int sm_count, cudaStream_t st, bool fieldless_zero) {
+  const int fz = fieldless_zero ? 1 : 0;
   if (a.n <= 0) return cudaSuccess;
   const int blocks = tc_grid(a.n, sm_count);
   cudaError_t e = cudaSuccess;
   switch (order) {
-    case 1: e = tc_configure(predict_tc_kernel<1>); if (e == cudaSuccess) predict_tc_kernel<1><<<blocks, kTcThreads, kTcSmemBytes, st>>>(a, P, pred); break;
-    case 2: e = tc_configure(predict_tc_kernel<2>); if (e == cudaSuccess) predict_tc_kernel<2><<<blocks, kTcThreads, kTcSmemBytes, st>>>(a, P, pred); break;
-    case 3: e = tc_configure(predict_tc_kernel<3>); if (e == cudaSuccess) predict_tc_kernel<3><<<blocks, kTcThreads, kTcSmemBytes, st>>>(a, P, pred); break;
-    case 4: e = tc_configure(predict_tc_kernel<4>); if (e == cudaSuccess) predict_tc_kernel<4><<<blocks, kTcThreads, kTcSmemBytes, st>>>(a, P, pred); break;
-    case 5: e = tc_configure(predict_tc_kernel<5>); if (e == cudaSuccess) predict_tc_kernel<5><<<blocks, kTcThreads, kTcSmemBytes, st>>>(a, P, pred); break;
+    case 1: e = tc_configure(predict_tc_kernel<1>); if (e == cudaSuccess) predict_tc_kernel<1><<<blocks, kTcThreads, kTcSmemBytes, st>>>(a, P, pred, fz); break;
+    case 2: e = tc_configure(predict_tc_kernel<2>); if (e == cudaSuccess) predict_tc_kernel<2><<<blocks, kTcThreads, kTcSmemBytes, st>>>(a, P, pred, fz); break;
+    case 3: e = tc_configure(predict_tc_kernel<3>); if (e == cudaSuccess) predict_tc_kernel<3><<<blocks, kTcThreads, kTcSmemBytes, st>>>(a, P, pred, fz); break;
+    case 4: e = tc_configure(predict_tc_kernel<4>); if (e == cudaSuccess) predict_tc_kernel<4><<<blocks, kTcThreads, kTcSmemBytes, st>>>(a, P, pred, fz); break;
+    case 5: e = tc_configure(predict_tc_kernel<5>); if (e == cudaSuccess) predict_tc_kernel<5><<<blocks, kTcThreads, kTcSmemBytes, st>>>(a, P, pred, fz); break;
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;

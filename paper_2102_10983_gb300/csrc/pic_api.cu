@@ -828,7 +828,7 @@ extern "C" int pic_push_step(pic_ctx* c, int64_t n, int64_t n_steps, pic_step_st
             ++launches;
             if (e == cudaSuccess)
               e = launch_predict_fused(fa, p, mlp_device_params(c->mlp), c->pred, c->sm_count,
-                                       c->stream);
+                                       c->stream, /*fieldless_zero=*/true);
             ++launches;
             if (e == cudaSuccess)
               e = launch_bin_predicted(c->pred, c->status, c->n, a.parity_cur, kPredMinK,

@@ -239,9 +239,11 @@ cudaError_t launch_mlp_infer(const float* P, const float* phi, int64_t n, uint8_
                              int sm_count, cudaStream_t s);
 // Features of step a's levels (theta = 3/2; a.halfE / a.halfB: the feature
 // nodes) and the predicted class of every particle in one pass (the same
-// predictions as features + launch_mlp_infer).
+// predictions as features + launch_mlp_infer).  fieldless_zero: a particle
+// that sees no field (E_y = B_z = 0 at its position) gets class 0 without the
+// network, and a tile of such particles skips the network.
 cudaError_t launch_predict_fused(const PushArgsMixed& a, int order, const float* P, uint8_t* pred,
-                                 int sm_count, cudaStream_t s);
+                                 int sm_count, cudaStream_t s, bool fieldless_zero = false);
 cudaError_t launch_mlp_grad(const float* P, const float* phi, const uint8_t* label, int64_t n,
                             float* grad, float* loss, int sm_count, cudaStream_t s);
 cudaError_t launch_mlp_adam(float* P, const float* grad, float* m1, float* m2, float lr, int step,

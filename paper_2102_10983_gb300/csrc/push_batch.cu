@@ -227,9 +227,12 @@ __global__ void batch_prefix_kernel(const int32_t* qcount_in, int32_t n_ens, int
 // Block shape of the batched kernel (its own: two blocks of eight warps per SM).
 constexpr int kBatchThreads = 256;
 constexpr int kBatchWarps = kBatchThreads / 32;
+#ifndef PIC_BATCH_MIN_BLOCKS
+#define PIC_BATCH_MIN_BLOCKS 2
+#endif
 
 template <int P>
-__global__ void __launch_bounds__(kBatchThreads, 2) push_batch_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(kBatchThreads, PIC_BATCH_MIN_BLOCKS) push_batch_kernel(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   BatchStash* stashes = reinterpret_cast<BatchStash*>(smem);  // [kBatchWarps][kStashK]
   __shared__ unsigned long long sh[12];
