@@ -437,6 +437,12 @@ int pic_push_mixed_noalloc(const pic_params* prm, int64_t n_particles, int32_t* 
                            const int64_t* level_i0, int64_t window_cells, int64_t n0,
                            int64_t n_steps, void* stream, pic_step_stats* stats);
 
+/* Set the error word of pic_push_mixed_noalloc's array on the current device
+ * to `word` (queued on `stream`), as a bounded device wait that gives up does,
+ * so that a host program can check its handling of PIC_ETIMEOUT without making
+ * a device wait run out.  Errors: PIC_ECUDA. */
+int pic_noalloc_inject_error(int32_t word, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

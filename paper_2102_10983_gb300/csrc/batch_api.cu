@@ -39,6 +39,7 @@ struct pic_batch {
   int32_t* qcount = nullptr;  // 2 x n_ens x 8, then cursor, blocks done
   int64_t* prefix = nullptr;  // 7 n_ens + 1
   float* half = nullptr;      // 2 x n_ens x W
+  float* coef = nullptr;      // 2 (step parity) x n_ens x W x 2(p+1): node coefficient tables
   std::vector<int64_t> slot_level;
   cudaGraphExec_t graph = nullptr;
   bool timing = false;
@@ -68,7 +69,7 @@ static void batch_free(pic_batch* b) {
   for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
   void* ptrs[] = {b->ens_dev, b->cell, b->frac, b->px, b->py, b->pz, b->status, b->ring,
                   b->slot_i0, b->i0_dev, b->staging, b->wtab64, b->wtab32, b->dstats,
-                  b->queue, b->qcount, b->prefix, b->half};
+                  b->queue, b->qcount, b->prefix, b->half, b->coef};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -133,6 +134,7 @@ extern "C" int pic_batch_create(const pic_ensemble* ens, int32_t n_ens, int32_t 
   A((void**)&b->qcount, sizeof(int32_t) * (2 * 8 * (size_t)n_ens + 8));
   A((void**)&b->prefix, sizeof(int64_t) * (7 * (size_t)n_ens + 1));
   A((void**)&b->half, sizeof(float) * 2 * (size_t)n_ens * window_cells);
+  A((void**)&b->coef, sizeof(float) * 2 * (size_t)n_ens * window_cells * 2 * (size_t)(order + 1));
   if (e != cudaSuccess) {
     batch_free(b);
     delete b;
@@ -369,6 +371,10 @@ static int queue_steps(pic_batch* b, int64_t n, int64_t n_steps) {
     a.parity_cur = (int)(j & 1);
     a.parity_next = (int)((j + 1) & 1);
     a.finalize = fin ? 1 : 0;
+    // node tables by step parity; the closing launch finishes step s with its own
+    const int64_t table = b->n_ens * b->W * 2 * (p + 1);
+    a.coef = b->coef + (s & 1) * table;
+    a.coef_p = (j > 0 && !fin) ? b->coef + ((s - 1) & 1) * table : a.coef;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (b->timing && !fin) {
       int rc = batch_timing_pair(b, &e0, &e1);

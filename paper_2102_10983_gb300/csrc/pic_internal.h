@@ -186,6 +186,11 @@ struct BatchArgs {
   int32_t* qcount_out;
   const int64_t* prefix;  // [7*n_ens + 1] heavy-item prefix (filled per launch)
   float* half;            // [2][n_ens][W]: E_y, B_z of every node at t_n (filled per launch)
+  // [n_ens][W][2(p+1)]: every node's monomial coefficients of the temporal
+  // interpolant (E_y then B_z) of this step (coef, filled per launch) and of
+  // the previous one (coef_p); two such tables, by step parity
+  float* coef;
+  const float* coef_p;
   int* cursor;
   unsigned* blocks_done;
   int parity_cur, parity_next, finalize;

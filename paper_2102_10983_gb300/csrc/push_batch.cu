@@ -35,7 +35,8 @@ __device__ __forceinline__ void ens_fields(const BatchArgs& a, const EnsDev& e, 
     lo = o > lo ? o : lo;
     hi = o + a.lstride - 1 < hi ? o + a.lstride - 1 : hi;
   }
-  F.coef = nullptr;  // coefficients formed from the levels
+  // the step's node table of this ensemble (batch_halfstep_kernel)
+  F.coef = (prev ? a.coef_p : a.coef) + (int64_t)(&e - a.ens) * a.lstride * (2 * (P + 1));
   F.lo = (int32_t)lo;
   F.hi = (int32_t)hi;
 }
@@ -79,7 +80,7 @@ __device__ __forceinline__ void batch_stash_drain(const BatchArgs& a, BatchStash
     ens_fields<P>(a, e, false, F);
     MixedState s = {S.cell[lane], S.frac[lane], S.ux[lane], S.uy[lane], S.uz[lane]};
     const int32_t i = S.idx[lane];
-    const bool ok = subcycle_f32<P>(F, a.wtab, a.mask, e.dt, e.inv_dx, e.qm, e.field_time, a.mono,
+    const bool ok = subcycle_f32<P, true, true>(F, a.wtab, a.mask, e.dt, e.inv_dx, e.qm, e.field_time, a.mono,
                                     k, S.kp[lane], 0.f, s);
     normalize(s);
     a.cell[i] = s.cell;
@@ -121,7 +122,7 @@ __device__ __forceinline__ void batch_heavy(const BatchArgs& a, int ens, int64_t
   const int k = deferred_k(st);
   const int k_prev = st & 7;
   MixedState s = {a.cell[i], a.frac[i], a.px[i], a.py[i], a.pz[i]};
-  const bool ok = subcycle_f32<P>(Fp, a.wtab, a.mask, e.dt, e.inv_dx, e.qm, e.field_time, a.mono,
+  const bool ok = subcycle_f32<P, true, true>(Fp, a.wtab, a.mask, e.dt, e.inv_dx, e.qm, e.field_time, a.mono,
                                   k, k_prev, 0.f, s);
   normalize(s);
   bool lost = !ok;
@@ -139,7 +140,7 @@ __device__ __forceinline__ void batch_heavy(const BatchArgs& a, int ens, int64_t
                                       e.k_max, capped, b0);
       count_step(tc, sh, kn, capped);
       if (kn < kDeferMin) {
-        const bool ok2 = subcycle_f32<P>(Fc, a.wtab, a.mask, e.dt, e.inv_dx, e.qm, e.field_time,
+        const bool ok2 = subcycle_f32<P, true, true>(Fc, a.wtab, a.mask, e.dt, e.inv_dx, e.qm, e.field_time,
                                          a.mono, kn, k, b0, s);
         normalize(s);
         lost = !ok2;
@@ -165,7 +166,10 @@ __device__ __forceinline__ void batch_heavy(const BatchArgs& a, int ens, int64_t
 }
 
 // Every ensemble's window nodes at t_n (theta = 1/2 weights): the same FMA
-// chain as a full gather takes at one node (see halfstep_kernel).
+// chain as a full gather takes at one node (see halfstep_kernel); and every
+// node's monomial coefficients of the temporal interpolant (to_monomial, the
+// values the sub-cycles would form from the levels), so that a sub-cycle reads
+// two 16-byte rows per grid instead of forming them.
 template <int P>
 __global__ void batch_halfstep_kernel(BatchArgs a) {
   constexpr int stride = 2 * (P + 1);
@@ -188,6 +192,20 @@ __global__ void batch_halfstep_kernel(BatchArgs a) {
     }
     a.half[q] = fe;
     a.half[total + q] = fb;
+    StepFields<P, true> F;
+    F.E.base = e.ringE + a.start_cur * W;
+    F.B.base = e.ringB + a.start_cur * W;
+    F.E.lstride = (int32_t)W;
+    F.B.lstride = (int32_t)W;
+    float e0[P + 1], e1[P + 1], b0[P + 1], b1[P + 1];
+    to_monomial<P>(F.E, (int32_t)c, (int32_t)c, a.mono[0], e0, e1);
+    to_monomial<P>(F.B, (int32_t)c, (int32_t)c, a.mono[1], b0, b1);
+    float* r = a.coef + q * stride;
+#pragma unroll
+    for (int k = 0; k <= P; ++k) {
+      r[k] = e0[k];
+      r[P + 1 + k] = b0[k];
+    }
   }
 }
 

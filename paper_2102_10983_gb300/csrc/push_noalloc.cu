@@ -257,3 +257,20 @@ extern "C" int pic_push_mixed_noalloc(const pic_params* prm, int64_t n_particles
   if (stats->clamped) return fail(PIC_EKMAX, "criterion capped at k_max");
   return PIC_OK;
 }
+
+extern "C" int pic_noalloc_inject_error(int32_t word, void* stream) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return fail(PIC_ECUDA, "pic_noalloc_inject_error: no usable current CUDA device");
+  DeviceSlot* slot = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_mutex);
+    int rc = scratch_on_current_device(dev, &slot);
+    if (rc != PIC_OK) return rc;
+  }
+  // pageable source: the copy is staged before cudaMemcpyAsync returns
+  cudaError_t e = cudaMemcpyAsync(&slot->ptr->stats.error, &word, sizeof(int32_t),
+                                  cudaMemcpyHostToDevice, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(PIC_ECUDA, cudaGetErrorString(e));
+  return PIC_OK;
+}

@@ -111,6 +111,7 @@ SIGNATURES = {
     "pic_push_step": (ctypes.c_int, [_VP, _I64, _I64, ctypes.POINTER(PicStepStats)]),
     "pic_stats_read": (ctypes.c_int, [_VP, ctypes.POINTER(PicStepStats), _I32]),
     "pic_finish": (ctypes.c_int, [_VP]),
+    "pic_noalloc_inject_error": (ctypes.c_int, [_I32, _VP]),
     "pic_set_stream": (ctypes.c_int, [_VP, _VP]),
     "pic_timing_enable": (ctypes.c_int, [_VP, _I32]),
     "pic_timing_read": (ctypes.c_int, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_I64), _I32]),

@@ -183,3 +183,30 @@ def test_noalloc_rejects_more_particles_than_its_scratch_holds():
                                              org.ctypes.data, 1024, 0, 1, None, None)
     assert rc == native.PIC_EINVAL
     assert b"65,536" in native.lib().pic_last_error(None)
+
+
+def test_noalloc_reports_a_set_error_word_once():
+    """The array's error word, set from the host as a giving-up wait would set
+    it: an asynchronous call (stats NULL) returns PIC_OK, the next call with
+    stats returns PIC_ETIMEOUT with the word, and the one after it is clean."""
+    wl = _wl(2048)
+    run = NoAllocRun(wl, 60)
+    run.call(0, 20)
+    assert native.lib().pic_noalloc_inject_error(7, run.stream) == native.PIC_OK
+    assert run.call(20, 20, want_stats=False) is None
+    prm = native.PicParams(wl.dt, wl.dx, wl.psi_max, -1.0, wl.order, 7, native.PIC_MIXED, 0,
+                           native.PIC_SCHED_BINNED)
+    p = wl.order
+    rows = range(40, 40 + p + 10)
+    Ep = (ctypes.c_void_p * len(rows))(*[run.Ed[r].data_ptr() for r in rows])
+    Bp = (ctypes.c_void_p * len(rows))(*[run.Bd[r].data_ptr() for r in rows])
+    org = np.ascontiguousarray([run.i0[r] for r in rows], dtype=np.int64)
+    st = native.PicStepStats()
+    d = run.d
+    rc = native.lib().pic_push_mixed_noalloc(
+        ctypes.byref(prm), wl.n_particles, d["cell"].data_ptr(), d["frac"].data_ptr(),
+        d["px"].data_ptr(), d["py"].data_ptr(), d["pz"].data_ptr(), d["status"].data_ptr(),
+        Ep, Bp, org.ctypes.data, wl.window, 40, 10, run.stream, ctypes.byref(st))
+    assert rc == native.PIC_ETIMEOUT and st.error == 7
+    assert b"gave up" in native.lib().pic_last_error(None)
+    assert run.call(50, 10)["error"] == 0
