@@ -22,9 +22,10 @@
 // warps, seven tiles in flight) share an SM: the chain of a tile (features,
 // three MMA round trips, three epilogues) is latency-bound, the SM is kept
 // busy by the other tiles.
-// One thread issues the MMAs and commits them to an mbarrier that every
-// thread waits on (a bounded wait: on a give-up the CTA records it, marks its
-// remaining predictions 0xFF, an invalid class, frees its TMEM and returns).
+// One thread issues the MMAs, commits them to an mbarrier and waits on it (a
+// bounded wait: on a give-up the CTA records it, marks its remaining
+// predictions 0xFF, an invalid class, frees its TMEM and returns); the other
+// threads wait at a CTA barrier, which takes no issue slots.
 //
 // Shared-memory operands use the no-swizzle K-major layout of 8 x 16-byte
 // core matrices: element (r, k) of an R x K tile sits at
@@ -140,6 +141,14 @@ __device__ __forceinline__ uint32_t bf2(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
+// max(lo, 0), max(hi, 0) rounded to BF16 and packed (lo in the low half): the
+// conversion's relu clamps a negative value to zero, in one instruction.
+__device__ __forceinline__ uint32_t bf2_relu(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
 // Packed FP32 master parameters (W1[64][6] b1[64] W2[64][64] b2[64] W3[8][64]
 // b3[8]) to BF16 operand tiles and FP32 biases.
 __device__ void tc_load_weights(TcSmem& s, const float* P) {
@@ -191,10 +200,15 @@ __device__ __forceinline__ void hidden_epilogue(TcSmem& s, uint32_t lane_addr, i
   for (int blk = 0; blk < 4; ++blk) {
     float v[16];
     tmem_ld16(lane_addr + (uint32_t)(c0 + 16 * blk), v);
+    const float2* b2 = reinterpret_cast<const float2*>(bias + 16 * blk);
+    uint32_t w[8];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = fmaxf(v[q] + bias[16 * blk + q], 0.f);
-    uint4 w0 = make_uint4(bf2(v[0], v[1]), bf2(v[2], v[3]), bf2(v[4], v[5]), bf2(v[6], v[7]));
-    uint4 w1 = make_uint4(bf2(v[8], v[9]), bf2(v[10], v[11]), bf2(v[12], v[13]), bf2(v[14], v[15]));
+    for (int q = 0; q < 8; ++q) {  // bias in paired FP32 adds, ReLU in the BF16 conversion
+      const float2 t = add2(make_float2(v[2 * q], v[2 * q + 1]), b2[q]);
+      w[q] = bf2_relu(t.x, t.y);
+    }
+    uint4 w0 = make_uint4(w[0], w[1], w[2], w[3]);
+    uint4 w1 = make_uint4(w[4], w[5], w[6], w[7]);
     *reinterpret_cast<uint4*>(s.A2[q] + cm_off(r, 16 * blk, kTcH)) = w0;
     *reinterpret_cast<uint4*>(s.A2[q] + cm_off(r, 16 * blk + 8, kTcH)) = w1;
   }
@@ -223,9 +237,12 @@ __device__ __forceinline__ int tc_tiles(TcSmem& s, const float (&f)[6], uint32_t
       mma_bf16(s.tmem + kTileCols * t, sdesc(saddr(s.A2[t]), 128, 256), sdesc(saddr(s.W1), 128, 256),
                idesc_bf16(kTcRows, kTcH), 0);
     mma_commit(&s.bar);
+    if (!bar_wait(&s.bar, ph) && !bar_wait(&s.bar, ph)) s.failed = 1;  // gives up after two waits
   }
-  if (ok) { ok = bar_wait(&s.bar, ph); ph ^= 1u; }
+  ph ^= 1u;
+  __syncthreads();  // the MMAs have completed (or the wait gave up) for every thread
   fence_after();
+  ok = !s.failed;
   if (ok) hidden_epilogue(s, lane_addr, 0, s.b1, q, r);
   fence_async_smem();
   fence_before();
@@ -242,9 +259,12 @@ __device__ __forceinline__ int tc_tiles(TcSmem& s, const float (&f)[6], uint32_t
         mma_bf16(s.tmem + kTileCols * t, sdesc(saddr(s.A2[t]) + 256u * k, 128, 1024),
                  sdesc(saddr(s.W2) + 256u * k, 128, 1024), idesc_bf16(kTcRows, kTcH), k > 0);
     mma_commit(&s.bar);
+    if (!bar_wait(&s.bar, ph) && !bar_wait(&s.bar, ph)) s.failed = 1;  // gives up after two waits
   }
-  if (ok) { ok = bar_wait(&s.bar, ph); ph ^= 1u; }
+  ph ^= 1u;
+  __syncthreads();
   fence_after();
+  ok = !s.failed;
   if (ok) hidden_epilogue(s, lane_addr, 0, s.b2, q, r);
   fence_async_smem();
   fence_before();
@@ -261,9 +281,12 @@ __device__ __forceinline__ int tc_tiles(TcSmem& s, const float (&f)[6], uint32_t
         mma_bf16(s.tmem + kTileCols * t, sdesc(saddr(s.A2[t]) + 256u * k, 128, 1024),
                  sdesc(saddr(s.W3) + 256u * k, 128, 1024), idesc_bf16(kTcRows, 16), k > 0);
     mma_commit(&s.bar);
+    if (!bar_wait(&s.bar, ph) && !bar_wait(&s.bar, ph)) s.failed = 1;  // gives up after two waits
   }
-  if (ok) { ok = bar_wait(&s.bar, ph); ph ^= 1u; }
+  ph ^= 1u;
+  __syncthreads();
   fence_after();
+  ok = !s.failed;
   int cls = 0xFF;
   if (ok) {
     float z[16];
