@@ -697,6 +697,17 @@ __device__ __forceinline__ FeatureInput feature_input(const PushArgsMixed& a, in
   return r;
 }
 
+// asinh x = sign(x) ln(|x| + sqrt(x^2 + 1)), with the special-function unit's
+// approximate reciprocal square root and logarithm (a few 1e-7 absolute, far
+// below the BF16 resolution of the network's input); exactly 0 at 0 (a
+// particle without field has zero field features).
+__device__ __forceinline__ float asinh_sfu(float x) {
+  const float a = fabsf(x);
+  const float t = __fmaf_rn(a, a, 1.0f);
+  const float r = copysignf(__logf(__fadd_rn(a, __fmul_rn(t, rsqrt_sfu(t)))), x);
+  return x == 0.f ? x : r;
+}
+
 __device__ __forceinline__ void features_of(const PushArgsMixed& a, const float* nodeE,
                                             const float* nodeB, int32_t lo, int32_t hi,
                                             const FeatureInput& in, float (&f)[6]) {
@@ -710,13 +721,13 @@ __device__ __forceinline__ void features_of(const PushArgsMixed& a, const float*
     const float* e = nodeE + (je & a.mask);
     const float* b = nodeB + (jb & a.mask);
     const float e0 = __ldg(e), e1 = __ldg(e + 1), b0 = __ldg(b), b1 = __ldg(b + 1);
-    f[0] = asinhf(fabsf(__fmaf_rn(we, __fsub_rn(e1, e0), e0)));
-    f[1] = asinhf(fabsf(__fmaf_rn(wb, __fsub_rn(b1, b0), b0)));
+    f[0] = asinh_sfu(fabsf(__fmaf_rn(we, __fsub_rn(e1, e0), e0)));
+    f[1] = asinh_sfu(fabsf(__fmaf_rn(wb, __fsub_rn(b1, b0), b0)));
   }
-  f[2] = asinhf(s.ux);
-  f[3] = asinhf(s.uy);
-  f[4] = asinhf(s.uz);
-  f[5] = 0.5f * log1pf(norm2(s.ux, s.uy, s.uz));
+  f[2] = asinh_sfu(s.ux);
+  f[3] = asinh_sfu(s.uy);
+  f[4] = asinh_sfu(s.uz);
+  f[5] = 0.5f * __logf(__fadd_rn(1.0f, norm2(s.ux, s.uy, s.uz)));  // log gamma
 }
 
 __device__ __forceinline__ void particle_features(const PushArgsMixed& a, const float* nodeE,
