@@ -202,7 +202,8 @@ int pic_finish(pic_ctx* ctx);
 /* Read (and optionally reset) the accumulated counters.  Synchronizes. */
 int pic_stats_read(pic_ctx* ctx, pic_step_stats* stats, int32_t reset);
 
-/* Replace the stream on which the context queues its work. */
+/* Replace the stream on which the context queues its work (with carried
+ * sub-cycles, after waiting for the old stream). */
 int pic_set_stream(pic_ctx* ctx, void* stream);
 
 /* Turn CUDA-event timing of the push on (1) or off (0).  When on, two events

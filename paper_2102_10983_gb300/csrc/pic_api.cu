@@ -321,6 +321,8 @@ extern "C" int pic_destroy(pic_ctx* c) {
 
 extern "C" int pic_set_stream(pic_ctx* c, void* stream) {
   if (!c) return PIC_EINVAL;
+  // carried sub-cycles continue on the new stream: what the old one holds first
+  if (c->open && (cudaStream_t)stream != c->stream) CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->stream = (cudaStream_t)stream;
   return PIC_OK;
 }

@@ -242,11 +242,17 @@ __global__ void batch_prefix_kernel(const int32_t* qcount_in, int32_t n_ens, int
   if (threadIdx.x == blockDim.x - 1) prefix[n] = acc;
 }
 
-// Block shape of the batched kernel (its own: two blocks of eight warps per SM).
-constexpr int kBatchThreads = 256;
+// Block shape of the batched kernel: four blocks of five warps per SM (20
+// warps at <= 102 registers, 93 used), measured faster than two of eight
+// (16 warps; 104 registers), three of six (18) and three of seven (21, with
+// spills) on the 512-ensemble workload: its serial sub-cycle chains want warps.
+#ifndef PIC_BATCH_THREADS
+#define PIC_BATCH_THREADS 160
+#endif
+constexpr int kBatchThreads = PIC_BATCH_THREADS;
 constexpr int kBatchWarps = kBatchThreads / 32;
 #ifndef PIC_BATCH_MIN_BLOCKS
-#define PIC_BATCH_MIN_BLOCKS 2
+#define PIC_BATCH_MIN_BLOCKS 4
 #endif
 
 template <int P>
