@@ -170,3 +170,24 @@ def test_upload_refuses_a_level_carried_work_needs():
     integ.pic_finish()
     assert upload(S - p + R) == native.PIC_OK
     integ.close()
+
+
+def test_stream_change_in_the_middle_of_a_carried_run():
+    """pic_set_stream while sub-cycles are carried: the library waits for the
+    old stream, the run continues on the new one with the plain bits."""
+    wl = _wl(3000)
+    a, sa = _plain(wl, 600, [1])
+    integ = _make(wl, native.PIC_SCHED_BINNED, [1], carry=1, heavy_budget=5)
+    s1 = H.run_gpu_calls(integ, wl, 3, 0, 300, [1])
+    other = torch.cuda.Stream()
+    integ.set_stream(other)
+    E, B, i0 = wl.levels(300, 300)
+    sb = _add(native.PicStepStats(), s1)
+    for r in range(300):  # level s, then step s, on the new stream
+        integ.pic_fields_upload(300 + r, i0[r], E[r], B[r])
+        st, _ = integ.pic_push_step(300 + r, 1, want_stats=True, ok=(0, 4, 5))
+        _add(sb, st)
+    b = integ.read_numpy()
+    _add(sb, integ.pic_stats_read(reset=True))
+    integ.close()
+    _same(a, sa, b, sb)
