@@ -191,3 +191,18 @@ def test_stream_change_in_the_middle_of_a_carried_run():
     _add(sb, integ.pic_stats_read(reset=True))
     integ.close()
     _same(a, sa, b, sb)
+
+
+@pytest.mark.parametrize("order", [1, 5])
+def test_carried_calls_other_orders(order):
+    """First and fifth order (p + 1 levels per step, ring order + 1 + carry +
+    the longest call), carry 2, budget 7."""
+    wl = _wl(2049, order=order)
+    a, sa = _plain(wl, 700, [1, 5], order=order)
+    integ = _make(wl, native.PIC_SCHED_BINNED, [1, 5], carry=2, heavy_budget=7, order=order)
+    sb = H.run_gpu_calls(integ, wl, order, 0, 700, [1, 5])
+    b = integ.read_numpy()
+    _add(sb, integ.pic_stats_read(reset=True))
+    integ.close()
+    assert sa.k_hist[4] > 0
+    _same(a, sa, b, sb)
