@@ -324,20 +324,7 @@ cudaError_t launch_bin_predicted(const uint8_t* pred, uint8_t* status, int64_t n
 // Dynamic shared memory of the binned kernel: the warps' stashes, then their
 // staged stream tiles.
 constexpr size_t kStashBytes = sizeof(Stash) * kWarps * kStashK;
-// Drain warps: the last PIC_DRAIN_WARPS warps of a block stream no more than
-// the one item they may have claimed and then push the batches of 32 parked
-// particles that the other (stream) warps hand them through per-drain-warp
-// mailboxes in shared memory (two each); a stream warp that finds no empty
-// mailbox pushes its batch itself.  0: every warp pushes its own stashes.
-#ifndef PIC_DRAIN_WARPS
-#define PIC_DRAIN_WARPS 0
-#endif
-constexpr int kDrainWarps = PIC_DRAIN_WARPS;
-constexpr int kStreamWarps = kWarps - kDrainWarps;
-constexpr int kMailboxes = 2 * kDrainWarps;
-static_assert(kDrainWarps >= 0 && kStreamWarps >= 1, "at least one stream warp per block");
-constexpr size_t kTilesBytes = sizeof(Tile) * kWarps * kStages;
-constexpr size_t kBinnedSmem = kStashBytes + kTilesBytes + sizeof(Stash) * kMailboxes;
+constexpr size_t kBinnedSmem = kStashBytes + sizeof(Tile) * kWarps * kStages;
 static_assert(kStashBytes % 128 == 0, "tiles start on a 128-byte boundary");
 
 // Two resident blocks per SM (of kThreads each): measured faster than three,
@@ -353,15 +340,9 @@ __global__ void __launch_bounds__(kThreads, PIC_BINNED_MIN_BLOCKS) push_binned_k
   extern __shared__ __align__(128) unsigned char smem[];
   Stash* stashes = reinterpret_cast<Stash*>(smem);  // [kWarps][kStashK]
   Tile* tiles = reinterpret_cast<Tile*>(smem + kStashBytes);  // [kWarps][kStages]
-  Stash* mail = reinterpret_cast<Stash*>(smem + kStashBytes + kTilesBytes);  // [kMailboxes]
   __shared__ __align__(8) uint64_t bars[kWarps * kStages];
   __shared__ unsigned long long sh[12];
   __shared__ int s_task[kWarps];
-  __shared__ int mail_state[kMailboxes > 0 ? kMailboxes : 1];  // 0 empty, 1 being filled, 2 full
-  __shared__ int mail_k[kMailboxes > 0 ? kMailboxes : 1];
-  __shared__ int streams_done;  // stream warps that have finished
-  if (threadIdx.x < kMailboxes) mail_state[threadIdx.x] = 0;
-  if (threadIdx.x == 0) streams_done = 0;
   __shared__ long long heavy_end[8];  // deferred items per k, largest k first (cumulative)
   __shared__ long long pred_end[8];   // then predicted items
   if (threadIdx.x < 12) sh[threadIdx.x] = 0ull;
@@ -424,63 +405,12 @@ __global__ void __launch_bounds__(kThreads, PIC_BINNED_MIN_BLOCKS) push_binned_k
     for (int r = 0; r < kStashK; ++r)
       if (r == q) stash_n[r] = v;
   };
-  const bool drain_warp = kDrainWarps > 0 && warp >= kStreamWarps;
-  // A stream warp hands the first 32 of its n >= 32 parked particles of stash
-  // q to a drain warp's empty mailbox (false: none was empty).  The entries
-  // are written, then the box is published (fence, state full); the drain
-  // warp reads them after seeing the state.
-  auto offload = [&](int q, int n) -> bool {
-    int box = -1;
-    if (lane == 0) {
-      for (int m = 0; m < kMailboxes; ++m)
-        if (atomicCAS(&mail_state[m], 0, 1) == 0) {
-          box = m;
-          break;
-        }
-    }
-    box = __shfl_sync(0xffffffffu, box, 0);
-    if (box < 0) return false;
-    Stash& S = my_stash[q];
-    Stash& M = mail[box];
-    M.idx[lane] = S.idx[lane];
-#ifndef PIC_STASH_INDEX_ONLY
-    M.cell[lane] = S.cell[lane];
-    M.frac[lane] = S.frac[lane];
-    M.ux[lane] = S.ux[lane];
-    M.uy[lane] = S.uy[lane];
-    M.uz[lane] = S.uz[lane];
-#endif
-    M.kp[lane] = S.kp[lane];
-    if (lane == 0) mail_k[box] = q + 1;
-    __syncwarp();
-    const int rest = n - 32;  // entries [32, n) to the front (n <= 64)
-    if (lane < rest) {
-      S.idx[lane] = S.idx[32 + lane];
-#ifndef PIC_STASH_INDEX_ONLY
-      S.cell[lane] = S.cell[32 + lane];
-      S.frac[lane] = S.frac[32 + lane];
-      S.ux[lane] = S.ux[32 + lane];
-      S.uy[lane] = S.uy[32 + lane];
-      S.uz[lane] = S.uz[32 + lane];
-#endif
-      S.kp[lane] = S.kp[32 + lane];
-    }
-    __syncwarp();
-    __threadfence_block();
-    if (lane == 0) atomicExch(&mail_state[box], 2);
-    return true;
-  };
   // push 32 particles of every stash that holds 32 or more (all = true: every
-  // parked particle), or hand them to a drain warp; one call site of the
-  // sub-cycle per call site of this
+  // parked particle); one call site of the sub-cycle per call site of this
   auto drain = [&](bool all) {
 #pragma unroll 1
     for (int q = 0; q < kStashK; ++q) {
       int n = stash_count(q);
-      if (kDrainWarps > 0 && !all && !drain_warp && n >= 32 && offload(q, n)) {
-        stash_set(q, n - 32);
-        continue;
-      }
       const int cnt = all ? n : (n >= 32 ? 32 : 0);
       if (cnt > 0) {
         stash_drain<P, RING>(a, F, my_stash[q], q + 1, n, cnt, sh);
@@ -727,14 +657,10 @@ __global__ void __launch_bounds__(kThreads, PIC_BINNED_MIN_BLOCKS) push_binned_k
     int64_t gen_next = (t - n_pred_end) * kTilesPerItem;
     int64_t gen_end = gen_next + kTilesPerItem < n_tiles ? gen_next + kTilesPerItem : n_tiles;
     bool gen_done = false;
-    if (!drain_warp) claim_ahead();  // a drain warp streams only the item it holds
+    claim_ahead();
     auto gen = [&]() -> int64_t {  // next tile of this warp, -1 when the stream is exhausted
       if (gen_done) return -1;
       if (gen_next >= gen_end) {
-        if (drain_warp) {
-          gen_done = true;
-          return -1;
-        }
         const int64_t it = take_ahead();
         if (it >= n_items) {
           gen_done = true;
@@ -804,52 +730,6 @@ __global__ void __launch_bounds__(kThreads, PIC_BINNED_MIN_BLOCKS) push_binned_k
   if (lane == 0) s_task[warp] = ahead;
   // push what is left in the stashes
   drain(true);
-  if (kDrainWarps > 0) {
-    if (!drain_warp) {
-      __threadfence_block();  // this warp's last handed-off box is published before it reports
-      if (lane == 0) atomicAdd(&streams_done, 1);
-    } else {
-      // push the boxes handed to this drain warp until every stream warp of the
-      // block has finished and its boxes are empty; a bounded wait (a stream
-      // warp that never finishes cannot occur: none of them waits on a drain warp)
-      const int box0 = 2 * (warp - kStreamWarps);
-      bool finishing = false;
-      for (uint32_t idle = 0;;) {
-        bool any = false;
-#pragma unroll 1
-        for (int m = box0; m < box0 + 2; ++m) {
-          int state = 0;
-          if (lane == 0) state = atomicAdd(&mail_state[m], 0);
-          state = __shfl_sync(0xffffffffu, state, 0);
-          if (state != 2) continue;
-          __threadfence_block();
-          const int k = *reinterpret_cast<volatile int*>(&mail_k[m]);
-          int n = 32;
-          stash_drain<P, RING>(a, F, mail[m], k, n, 32, sh);
-          __syncwarp();
-          if (lane == 0) atomicExch(&mail_state[m], 0);
-          any = true;
-        }
-        if (any) {
-          idle = 0;
-          continue;
-        }
-        if (finishing) break;
-        int sd = 0;
-        if (lane == 0) sd = atomicAdd(&streams_done, 0);
-        sd = __shfl_sync(0xffffffffu, sd, 0);
-        if (sd == kStreamWarps) {
-          finishing = true;  // one more look at the boxes, then leave
-          continue;
-        }
-        if (++idle > (1u << 21)) {
-          if (lane == 0) atomicExch(&a.stats->error, 3);
-          break;
-        }
-        __nanosleep(128);
-      }
-    }
-  }
   flush_counters(tc, sh, a.stats);
 
   // the last block to finish resets the cursor and the consumed queue counts
