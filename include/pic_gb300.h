@@ -317,6 +317,12 @@ int pic_batch_destroy(pic_batch* b);
  * non-NULL stream). */
 int pic_batch_config(pic_batch* b, int32_t chunk, int32_t blocks_per_sm, int32_t use_graph);
 
+/* Sub-steps a long (k >= 3) sub-cycle may take per particle and launch (as
+ * pic_params.heavy_budget: the rest continues in the next launch while the
+ * particle runs behind the stream, with the same bits; a call finishes every
+ * particle).  0: 1024; < 0: no limit.  Errors: PIC_EINVAL. */
+int pic_batch_heavy_budget(pic_batch* b, int32_t budget);
+
 /* Load / read all particles, concatenated in ensemble order (FP64 in and out,
  * mixed layout inside; status as for pic_particles_write). */
 int pic_batch_particles_write(pic_batch* b, const double* x, const double* px, const double* py,

@@ -40,6 +40,9 @@ struct pic_batch {
   int64_t* prefix = nullptr;  // 7 n_ens + 1
   float* half = nullptr;      // 2 x n_ens x W
   float* coef = nullptr;      // 2 (step parity) x n_ens x W x 2(p+1): node coefficient tables
+  int32_t* lag_step = nullptr;  // per particle: the step a deferred particle is in (call-relative)
+  uint16_t* lag_j = nullptr;    // and the sub-steps of it done
+  int32_t heavy_budget = 1024;  // sub-steps of long sub-cycles per particle and launch
   std::vector<int64_t> slot_level;
   cudaGraphExec_t graph = nullptr;
   bool timing = false;
@@ -69,7 +72,7 @@ static void batch_free(pic_batch* b) {
   for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
   void* ptrs[] = {b->ens_dev, b->cell, b->frac, b->px, b->py, b->pz, b->status, b->ring,
                   b->slot_i0, b->i0_dev, b->staging, b->wtab64, b->wtab32, b->dstats,
-                  b->queue, b->qcount, b->prefix, b->half, b->coef};
+                  b->queue, b->qcount, b->prefix, b->half, b->coef, b->lag_step, b->lag_j};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -135,6 +138,8 @@ extern "C" int pic_batch_create(const pic_ensemble* ens, int32_t n_ens, int32_t 
   A((void**)&b->prefix, sizeof(int64_t) * (7 * (size_t)n_ens + 1));
   A((void**)&b->half, sizeof(float) * 2 * (size_t)n_ens * window_cells);
   A((void**)&b->coef, sizeof(float) * 2 * (size_t)n_ens * window_cells * 2 * (size_t)(order + 1));
+  A((void**)&b->lag_step, cap * 4);
+  A((void**)&b->lag_j, cap * 2);
   if (e != cudaSuccess) {
     batch_free(b);
     delete b;
@@ -371,6 +376,11 @@ static int queue_steps(pic_batch* b, int64_t n, int64_t n_steps) {
     a.parity_cur = (int)(j & 1);
     a.parity_next = (int)((j + 1) & 1);
     a.finalize = fin ? 1 : 0;
+    a.lag_step = b->lag_step;
+    a.lag_j = b->lag_j;
+    a.step0 = n;
+    a.step_cur = fin ? s + 1 : s;  // the closing launch brings every particle to the end of s
+    a.heavy_budget = b->heavy_budget;
     // node tables by step parity; the closing launch finishes step s with its own
     const int64_t table = b->n_ens * b->W * 2 * (p + 1);
     a.coef = b->coef + (s & 1) * table;
@@ -533,3 +543,9 @@ extern "C" int pic_batch_autotune(pic_batch* b, int64_t n, int32_t steps, int32_
 }
 
 extern "C" const char* pic_batch_last_error(const pic_batch* b) { return b ? b->err : ""; }
+
+extern "C" int pic_batch_heavy_budget(pic_batch* b, int32_t budget) {
+  if (!b) return PIC_EINVAL;
+  b->heavy_budget = budget == 0 ? 1024 : budget;
+  return PIC_OK;
+}

@@ -194,6 +194,13 @@ struct BatchArgs {
   int* cursor;
   unsigned* blocks_done;
   int parity_cur, parity_next, finalize;
+  // resumable long sub-cycles, as in PushArgsMixed: a deferred particle is in
+  // step step0 + lag_step[i] with lag_j[i] of its sub-steps done; a deferred
+  // item spends at most heavy_budget sub-steps of long sub-cycles per launch
+  int32_t* lag_step;
+  uint16_t* lag_j;
+  int64_t step0, step_cur;
+  int32_t heavy_budget;  // <= 0: no limit
 };
 
 cudaError_t launch_batch_step(const BatchArgs& a, int order, int blocks, cudaStream_t s,

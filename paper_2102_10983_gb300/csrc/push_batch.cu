@@ -108,8 +108,48 @@ __device__ __forceinline__ void batch_stash_drain(const BatchArgs& a, BatchStash
   n = rest;
 }
 
-// Deferred particle i of ensemble ens: finish its previous step, then this
-// step's criterion (pushed at once if k < kDeferMin, else deferred again).
+// Field view of macro step s of ensemble e from its mirrored ring and the
+// device copy of its slots' window origins: for a deferred particle that runs
+// behind the stream (no node table).
+template <int P>
+__device__ __forceinline__ StepFields<P, true> ens_step_fields(const BatchArgs& a, const EnsDev& e,
+                                                               int64_t s) {
+  StepFields<P, true> F;
+  const int64_t R = a.R;
+  const int64_t start = ((s - P) % R + R) % R;
+  F.E.base = e.ringE + start * a.lstride;
+  F.B.base = e.ringB + start * a.lstride;
+  F.E.lstride = (int32_t)a.lstride;
+  F.B.lstride = (int32_t)a.lstride;
+  F.coef = nullptr;
+  int64_t lo = INT64_MIN, hi = INT64_MAX;
+#pragma unroll
+  for (int l = 0; l <= P; ++l) {
+    const int64_t o = e.slot_i0[(start + l) % R];
+    lo = o > lo ? o : lo;
+    hi = o + a.lstride - 1 < hi ? o + a.lstride - 1 : hi;
+  }
+  F.lo = (int32_t)lo;
+  F.hi = (int32_t)hi;
+  return F;
+}
+
+__device__ __forceinline__ void batch_defer_mark(const BatchArgs& a, int64_t i, int k_prev, int k,
+                                                 int64_t s, int j = 0) {
+  a.status[i] = (uint8_t)(k_prev | (k << 4));
+  a.lag_step[i] = (int32_t)(s - a.step0);
+  a.lag_j[i] = (uint16_t)j;
+}
+
+// Deferred particle i of ensemble ens (the batched form of heavy_particle):
+// it is in step step0 + lag_step[i] with lag_j[i] of its sub-steps done.
+// Finish that step and, if it ran behind the stream, every step up to the
+// previous one (taking each step's criterion), spending at most heavy_budget
+// sub-steps of long sub-cycles; then take the current step's criterion:
+// pushed at once if k < kDeferMin, else deferred again.  Out of budget: it
+// stays deferred where it is and resumes in the next launch.  finalize: bring
+// it to the end of the last step only (public status).  key: ens * 8 + k of
+// a re-deferral, else -1.
 template <int P>
 __device__ __forceinline__ void batch_heavy(const BatchArgs& a, int ens, int64_t i,
                                             const float* wcrit, ThreadCounters& tc,
@@ -118,50 +158,110 @@ __device__ __forceinline__ void batch_heavy(const BatchArgs& a, int ens, int64_t
   const EnsDev& e = a.ens[ens];
   StepFields<P, true> Fp, Fc;
   ens_fields<P>(a, e, true, Fp);
+  ens_fields<P>(a, e, false, Fc);
   const uint8_t st = a.status[i];
-  const int k = deferred_k(st);
-  const int k_prev = st & 7;
+  int k = deferred_k(st);
+  int k_prev = st & 7;
   MixedState s = {a.cell[i], a.frac[i], a.px[i], a.py[i], a.pz[i]};
-  const bool ok = subcycle_f32<P, true, true>(Fp, a.wtab, a.mask, e.dt, e.inv_dx, e.qm, e.field_time, a.mono,
-                                  k, k_prev, 0.f, s);
-  normalize(s);
-  bool lost = !ok;
-  uint8_t out = (uint8_t)k;
-  if (ok && !a.finalize) {
-    ens_fields<P>(a, e, false, Fc);
-    int32_t je, jb;
-    float we, wb;
-    if (!tent_coords(s.cell, s.frac, Fc.lo, Fc.hi, je, we, jb, wb)) {
-      lost = true;
+  int64_t si = a.step0 + a.lag_step[i];
+  int j0 = a.lag_j[i];
+  int budget = !a.finalize && a.heavy_budget > 0 ? a.heavy_budget : INT_MAX;
+  float b0 = 0.f;  // the criterion's B_z of step si (used when k = 0)
+  auto store = [&]() {
+    a.cell[i] = s.cell;
+    a.frac[i] = s.frac;
+    a.px[i] = s.ux;
+    a.py[i] = s.uy;
+    a.pz[i] = s.uz;
+  };
+  auto lose = [&]() {
+    store();
+    a.status[i] = (uint8_t)(k | PIC_STATUS_LOST);
+    atomicAdd(&sh[11], 1ull);
+  };
+  for (;;) {
+    // sub-steps j0+1 .. j1 of step si
+    const int m = 1 << (2 * k);
+    int j1 = m;
+    if (k >= kDeferMin && m - j0 > budget) j1 = j0 + budget;
+    bool ok;
+    if (si >= a.step_cur - 1) {  // the previous or the current step: node tables
+      const StepFields<P, true> Fs = si == a.step_cur ? Fc : Fp;
+      ok = subcycle_f32<P, true, true>(Fs, a.wtab, a.mask, e.dt, e.inv_dx, e.qm, e.field_time, a.mono,
+                                       k, k_prev, b0, s, j0, j1);
     } else {
+      const StepFields<P, true> Fs = ens_step_fields<P>(a, e, si);
+      ok = subcycle_f32<P, true, false>(Fs, a.wtab, a.mask, e.dt, e.inv_dx, e.qm, e.field_time,
+                                        a.mono, k, k_prev, b0, s, j0, j1);
+    }
+    if (k >= kDeferMin) budget -= j1 - j0;
+    if (!ok) {
+      lose();
+      return;
+    }
+    if (j1 < m) {  // out of budget inside the sub-cycle: resume here next launch
+      store();
+      batch_defer_mark(a, i, k_prev, k, si, j1);
+      key = ens * 8 + k;
+      return;
+    }
+    normalize(s);
+    if (si == a.step_cur) {  // the current step's short sub-cycle is done
+      store();
+      a.status[i] = (uint8_t)(k | (a.parity_next ? kParity : 0));
+      return;
+    }
+    if (si == a.step_cur - 1) {
+      if (a.finalize) {
+        store();
+        a.status[i] = (uint8_t)k;
+        return;
+      }
+      int32_t je, jb;
+      float we, wb;
+      if (!tent_coords(s.cell, s.frac, Fc.lo, Fc.hi, je, we, jb, wb)) {
+        lose();
+        return;
+      }
       bool capped;
-      float b0;
       const int kn = criterion_f32<P>(Fc.B, wcrit, jb, wb, a.mask, s, e.qm_abs, e.dt, e.psi_max,
                                       e.k_max, capped, b0);
       count_step(tc, sh, kn, capped);
-      if (kn < kDeferMin) {
-        const bool ok2 = subcycle_f32<P, true, true>(Fc, a.wtab, a.mask, e.dt, e.inv_dx, e.qm, e.field_time,
-                                         a.mono, kn, k, b0, s);
-        normalize(s);
-        lost = !ok2;
-        out = (uint8_t)(kn | (a.parity_next ? kParity : 0));
-        if (lost) out = (uint8_t)kn;
-      } else {
-        out = (uint8_t)(k | (kn << 4));
+      if (kn >= kDeferMin) {
+        store();
+        batch_defer_mark(a, i, k, kn, a.step_cur);
         key = ens * 8 + kn;
+        return;
       }
+      // a short sub-cycle of the current step: the next pass of the loop
+      k_prev = k;
+      k = kn;
+      si = a.step_cur;
+      j0 = 0;
+      continue;
     }
-  }
-  a.cell[i] = s.cell;
-  a.frac[i] = s.frac;
-  a.px[i] = s.ux;
-  a.py[i] = s.uy;
-  a.pz[i] = s.uz;
-  if (lost) {
-    a.status[i] = (uint8_t)((out & 7) | PIC_STATUS_LOST);
-    atomicAdd(&sh[11], 1ull);
-  } else {
-    a.status[i] = out;
+    // behind the stream: the next step's criterion, then its sub-cycle
+    si += 1;
+    const StepFields<P, true> Fs = si == a.step_cur - 1 ? Fp : ens_step_fields<P>(a, e, si);
+    int32_t je, jb;
+    float we, wb;
+    if (!tent_coords(s.cell, s.frac, Fs.lo, Fs.hi, je, we, jb, wb)) {
+      lose();
+      return;
+    }
+    bool capped;
+    const int kn = criterion_f32<P>(Fs.B, wcrit, jb, wb, a.mask, s, e.qm_abs, e.dt, e.psi_max,
+                                    e.k_max, capped, b0);
+    count_step(tc, sh, kn, capped);
+    k_prev = k;
+    k = kn;
+    j0 = 0;
+    if (k >= kDeferMin && budget <= 0) {
+      store();
+      batch_defer_mark(a, i, k_prev, k, si);
+      key = ens * 8 + k;
+      return;
+    }
   }
 }
 
@@ -367,7 +467,7 @@ __global__ void __launch_bounds__(kBatchThreads, PIC_BATCH_MIN_BLOCKS) push_batc
           } else if (k < kDeferMin) {
             sk = k;
           } else {
-            a.status[i] = (uint8_t)(k_prev | (k << 4));
+            batch_defer_mark(a, i, k_prev, k, a.step_cur);
             key = ens * 8 + k;
           }
         }

@@ -111,6 +111,7 @@ SIGNATURES = {
     "pic_push_step": (ctypes.c_int, [_VP, _I64, _I64, ctypes.POINTER(PicStepStats)]),
     "pic_stats_read": (ctypes.c_int, [_VP, ctypes.POINTER(PicStepStats), _I32]),
     "pic_finish": (ctypes.c_int, [_VP]),
+    "pic_batch_heavy_budget": (ctypes.c_int, [_VP, _I32]),
     "pic_noalloc_inject_error": (ctypes.c_int, [_I32, _VP]),
     "pic_set_stream": (ctypes.c_int, [_VP, _VP]),
     "pic_timing_enable": (ctypes.c_int, [_VP, _I32]),
@@ -438,6 +439,9 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+    def heavy_budget(self, budget: int):
+        self._chk(lib().pic_batch_heavy_budget(self.h, int(budget)))
 
     def config(self, chunk=256, blocks_per_sm=2, use_graph=False):
         self._chk(lib().pic_batch_config(self.h, int(chunk), int(blocks_per_sm), 1 if use_graph else 0))

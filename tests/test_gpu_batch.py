@@ -66,11 +66,13 @@ def _single(wl, kmax, ft, steps, calls):
     return out, agg
 
 
-def _batch(ens, steps, calls, graph=False, tune=False):
+def _batch(ens, steps, calls, graph=False, tune=False, budget=0):
     b = native.Batch([dict(dt=wl.dt, dx=wl.dx, psi_max=wl.psi_max, k_max=kmax, field_time=ft,
                            n_particles=wl.n_particles) for wl, kmax, ft in ens],
                      order=3, window=WIN, ring_levels=3 + 2 + max(calls),
                      stream=torch.cuda.current_stream())
+    if budget:
+        b.heavy_budget(budget)
     inis = [wl.particles() for wl, _, _ in ens]
     cat = [np.concatenate([getattr(i, f) for i in inis]) for f in ("x", "px", "py", "pz")]
     b.particles_write(*cat)
@@ -109,11 +111,13 @@ def _batch(ens, steps, calls, graph=False, tune=False):
     return out, agg, tuned
 
 
-@pytest.mark.parametrize("calls", [[1], [13, 40]])
-def test_batch_bitwise_equals_single_contexts(calls):
+@pytest.mark.parametrize("calls,budget", [([1], 0), ([13, 40], 0), ([13, 40], 5), ([40], -1)])
+def test_batch_bitwise_equals_single_contexts(calls, budget):
+    """Budgets of 5 sub-steps per launch (long sub-cycles resumed over many
+    launches, particles running behind the stream) and no limit."""
     ens = _ensembles()
     steps = 600
-    got, gagg, _ = _batch(ens, steps, calls)
+    got, gagg, _ = _batch(ens, steps, calls, budget=budget)
     off = 0
     tot = np.zeros(12, dtype=np.int64)
     for wl, kmax, ft in ens:
