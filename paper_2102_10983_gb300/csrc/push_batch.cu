@@ -360,7 +360,6 @@ __global__ void __launch_bounds__(kBatchThreads, PIC_BATCH_MIN_BLOCKS) push_batc
   extern __shared__ __align__(16) unsigned char smem[];
   BatchStash* stashes = reinterpret_cast<BatchStash*>(smem);  // [kBatchWarps][kStashK]
   __shared__ unsigned long long sh[12];
-  __shared__ int s_task[kBatchWarps];
   if (threadIdx.x < 12) sh[threadIdx.x] = 0ull;
   __syncthreads();
   constexpr int stride = 2 * (P + 1);
@@ -379,12 +378,16 @@ __global__ void __launch_bounds__(kBatchThreads, PIC_BATCH_MIN_BLOCKS) push_batc
   const int64_t n_items = n_heavy + (a.finalize ? 0 : a.n_chunks);
   const int per_lane = a.chunk / 32;
 
+  // work items from the cursor, each claimed one item ahead (lane 0 holds the
+  // claim), so the atomic's round trip overlaps the current item's work; the
+  // value that ends the loop is the last claim, consumed before the block
+  // reports done (the last block resets the cursor)
+  int ahead = 0;
+  if (lane == 0) ahead = atomicAdd(a.cursor, 1);
   for (;;) {
-    if (lane == 0) s_task[warp] = atomicAdd(a.cursor, 1);
-    __syncwarp();
-    const int64_t t = s_task[warp];
-    __syncwarp();
+    const int64_t t = __shfl_sync(0xffffffffu, ahead, 0);
     if (t >= n_items) break;
+    if (lane == 0) ahead = atomicAdd(a.cursor, 1);
     if (t < n_heavy) {
       int lo = 0, hi = 7 * a.n_ens - 1;  // last entry q with prefix[q] <= t
       while (lo < hi) {
