@@ -378,16 +378,18 @@ __global__ void __launch_bounds__(kBatchThreads, PIC_BATCH_MIN_BLOCKS) push_batc
   const int64_t n_items = n_heavy + (a.finalize ? 0 : a.n_chunks);
   const int per_lane = a.chunk / 32;
 
-  // work items from the cursor, each claimed one item ahead (lane 0 holds the
-  // claim), so the atomic's round trip overlaps the current item's work; the
-  // value that ends the loop is the last claim, consumed before the block
-  // reports done (the last block resets the cursor)
+  // work items from the cursor (lane 0 holds the claim); in the stream the
+  // next item is claimed while the current chunk is pushed, so the atomic's
+  // round trip overlaps its work (a deferred item claims after it is done: two
+  // long sub-cycles are never bound to one warp); the value that ends the loop
+  // is the last claim, consumed before the block reports done (the last block
+  // resets the cursor)
   int ahead = 0;
   if (lane == 0) ahead = atomicAdd(a.cursor, 1);
   for (;;) {
     const int64_t t = __shfl_sync(0xffffffffu, ahead, 0);
     if (t >= n_items) break;
-    if (lane == 0) ahead = atomicAdd(a.cursor, 1);
+    if (t >= n_heavy && lane == 0) ahead = atomicAdd(a.cursor, 1);
     if (t < n_heavy) {
       int lo = 0, hi = 7 * a.n_ens - 1;  // last entry q with prefix[q] <= t
       while (lo < hi) {
@@ -403,6 +405,7 @@ __global__ void __launch_bounds__(kBatchThreads, PIC_BATCH_MIN_BLOCKS) push_batc
         batch_heavy<P>(a, ens, i, wcrit, tc, sh, key);
       }
       batch_enqueue(a, key, i);
+      if (lane == 0) ahead = atomicAdd(a.cursor, 1);
       continue;
     }
     // stream chunk: which ensemble, which particles
