@@ -360,6 +360,7 @@ __global__ void __launch_bounds__(kBatchThreads, PIC_BATCH_MIN_BLOCKS) push_batc
   extern __shared__ __align__(16) unsigned char smem[];
   BatchStash* stashes = reinterpret_cast<BatchStash*>(smem);  // [kBatchWarps][kStashK]
   __shared__ unsigned long long sh[12];
+  __shared__ int s_task[kBatchWarps];
   if (threadIdx.x < 12) sh[threadIdx.x] = 0ull;
   __syncthreads();
   constexpr int stride = 2 * (P + 1);
@@ -378,18 +379,12 @@ __global__ void __launch_bounds__(kBatchThreads, PIC_BATCH_MIN_BLOCKS) push_batc
   const int64_t n_items = n_heavy + (a.finalize ? 0 : a.n_chunks);
   const int per_lane = a.chunk / 32;
 
-  // work items from the cursor (lane 0 holds the claim); in the stream the
-  // next item is claimed while the current chunk is pushed, so the atomic's
-  // round trip overlaps its work (a deferred item claims after it is done: two
-  // long sub-cycles are never bound to one warp); the value that ends the loop
-  // is the last claim, consumed before the block reports done (the last block
-  // resets the cursor)
-  int ahead = 0;
-  if (lane == 0) ahead = atomicAdd(a.cursor, 1);
   for (;;) {
-    const int64_t t = __shfl_sync(0xffffffffu, ahead, 0);
+    if (lane == 0) s_task[warp] = atomicAdd(a.cursor, 1);
+    __syncwarp();
+    const int64_t t = s_task[warp];
+    __syncwarp();
     if (t >= n_items) break;
-    if (t >= n_heavy && lane == 0) ahead = atomicAdd(a.cursor, 1);
     if (t < n_heavy) {
       int lo = 0, hi = 7 * a.n_ens - 1;  // last entry q with prefix[q] <= t
       while (lo < hi) {
@@ -405,7 +400,6 @@ __global__ void __launch_bounds__(kBatchThreads, PIC_BATCH_MIN_BLOCKS) push_batc
         batch_heavy<P>(a, ens, i, wcrit, tc, sh, key);
       }
       batch_enqueue(a, key, i);
-      if (lane == 0) ahead = atomicAdd(a.cursor, 1);
       continue;
     }
     // stream chunk: which ensemble, which particles
